@@ -1,0 +1,352 @@
+"""Benchmark of the TREVR2 reverse ray trace on one GB300 (or N in replica).
+
+One step = one radiation step of the whole path on the clumpy multi-band
+field: tree build (Morton keys, sort, bisection, aggregates, per-direction
+absorption tables) + the walk giving J for every active receiver, 3 bands,
+192 HEALPix beams.  The metric is active-receiver x beam x band per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun), each rank runs an independent snapshot (seed + rank):
+weak scaling, no collective on the data path; the step time is the max over
+ranks.  `--impl reference` times the FP64 CPU oracle on a bounded sample.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "active receiver x HEALPix-ray x band / s"
+UNIT = "receiver*ray*band/s"
+NODE_BYTES = 32  # walk record of one node
+
+
+def _workload_name(case):
+    n_gas = len(case["active"])
+    return (f"clumpy multi-band field: {n_gas:,} gas on a 128^3 jittered lattice (lognormal, "
+            f"sigma 1.5, P(k)~k^-3) + 10,000 power-law sources, 3 bands kappa (10, 3, 0.5), "
+            f"nside 4 (192 beams), theta 0.5, all gas active")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _algorithmic_bytes_per_receiver(stats, nb):
+    """Bytes a receiver's walk must touch by the method's own count:
+    N_visit node records, one absorption value per band per beam segment,
+    one source record (position + per-band luminosity) per source, and the
+    J row written."""
+    visited, cut, segments, sources = [stats[:, i].astype(np.float64) for i in range(4)]
+    per = visited * NODE_BYTES + segments * 4 * nb + sources * (12 + 4 * nb) + 4 * nb
+    return float(per.mean()), {k: float(v.mean()) for k, v in
+                               zip(("visited", "cut", "segments", "sources"),
+                                   (visited, cut, segments, sources))}
+
+
+def _oracle_sample(case, seconds_target, rng_seed=0):
+    """The FP64 oracle on a bounded sample of receivers (all host cores)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ot = oracle.OracleTree.from_case(case)
+    ot.alpha_table(case["nside"])  # builds and caches the tables
+    t_build = time.perf_counter() - t0
+    rng = np.random.default_rng(rng_seed)
+    pilot = rng.choice(case["active"], 256, replace=False)
+    t0 = time.perf_counter()
+    _, st_p = ot.J(pilot, case["nside"], case["theta"], nthreads=cores, stats=True)
+    t_p = time.perf_counter() - t0
+    n = int(min(len(case["active"]), max(256, seconds_target / max(t_p, 1e-6) * 256)))
+    sample = rng.choice(case["active"], n, replace=False)
+    t0 = time.perf_counter()
+    _, st = ot.J(sample, case["nside"], case["theta"], nthreads=cores, stats=True)
+    t_j = time.perf_counter() - t0
+    return ot, sample, st, t_j, t_build, cores
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    case = workloads.clumpy_multiband()
+    npix, nb = 12 * case["nside"] ** 2, case["nb"]
+    import oracle
+    cores = os.cpu_count() or 1
+    ot = oracle.OracleTree.from_case(case)
+    ot.alpha_table(case["nside"])
+    rng = np.random.default_rng(1)
+    per_step = args.reference_sample
+    times = []
+    for step in range(args.warmup + args.steps):
+        sample = rng.choice(case["active"], per_step, replace=False)
+        t0 = time.perf_counter()
+        ot.J(sample, case["nside"], case["theta"], nthreads=cores)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    t = float(np.mean(times))
+    value = per_step * npix * nb / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": _workload_name(case), "receivers_per_step": per_step,
+                   "beams": npix, "bands": nb},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} random receivers per step of the 2,097,152; "
+                                   f"tree and tables built once before timing"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_2310_15235_gb300 as t2
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    case = workloads.clumpy_multiband(seed=1003 + rank)
+    npix, nb = 12 * case["nside"] ** 2, case["nb"]
+    A = len(case["active"])
+    units = A * npix * nb
+
+    def to_dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    inp = {k: to_dev(case[k]) for k in ("pos", "mass", "kappa", "lum", "h", "active")}
+    J = torch.empty((A, nb), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev_walk=None):
+        tree = t2.build(inp["pos"], inp["mass"], inp["kappa"], inp["lum"], inp["h"],
+                        case["box_lo"], case["box_size"], case["bucket"], device=dev)
+        tree.prepare(case["nside"])  # per-direction tables: part of the step
+        if ev_walk is not None:
+            ev_walk[0].record(stream)
+        tree.J(inp["active"], case["nside"], case["theta"], out=J, flags=t2.ASYNC)
+        if ev_walk is not None:
+            ev_walk[1].record(stream)
+        tree.status()
+        tree.free()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = t2.kernel_launches()
+    walk_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(walk_events[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = t2.kernel_launches() - launches0
+    clk = clocks.stop()
+    total_ms = e0.elapsed_time(e1)
+    walk_ms = [a.elapsed_time(b) for a, b in walk_events]
+    ms_step = total_ms / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * units / (ms_step * 1e-3)
+
+    # End to end through the public API from pinned host buffers.
+    host = {k: torch.from_numpy(np.ascontiguousarray(case[k])).pin_memory()
+            for k in ("pos", "mass", "kappa", "lum", "h", "active")}
+    J_host = torch.empty((A, nb), dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = J_host.numel() * 4
+
+    def e2e_step():
+        d = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+        tree = t2.build(d["pos"], d["mass"], d["kappa"], d["lum"], d["h"], case["box_lo"],
+                        case["box_size"], case["bucket"], device=dev)
+        out = tree.J(d["active"], case["nside"], case["theta"])
+        J_host.copy_(out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        tree.free()
+
+    e2e_step()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * units / e2e_s
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    hbm_peak, peak_kind = _peaks()
+    walk_avg = float(np.mean(walk_ms))
+    roofline = None
+    cpu = None
+    extra = {}
+    if world == 1 and not args.no_cpu_baseline:
+        ot, sample, st, t_j, t_build, cores = _oracle_sample(case, args.cpu_seconds)
+        per_rec, means = _algorithmic_bytes_per_receiver(st, nb)
+        achieved = per_rec * A / (walk_avg * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": None,
+                    "kernel": "k_walk", "peak_kind": peak_kind,
+                    "algorithmic_bytes_per_unit": per_rec / (npix * nb),
+                    "per_receiver_counts": means}
+        cpu = {"value": len(sample) * npix * nb / t_j, "unit": UNIT, "cores": cores,
+               "kind": "oracle",
+               "sample": f"{len(sample)} random receivers of the same field (J walk only; "
+                         f"oracle tree+tables build {t_build:.1f} s not included)"}
+        # sampled parity of this very run
+        ref = ot.J(sample[:512], case["nside"], case["theta"], nthreads=cores)
+        idx = sample[:512]  # active == arange for this workload
+        got = J.cpu().numpy()[idx]
+        rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
+        extra["parity_sample"] = {"receivers": 512, "median_rel": float(np.median(rel)),
+                                  "max_rel": float(rel.max())}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": _workload_name(case), "receivers": A, "beams": npix, "bands": nb,
+                   "step": "tree build + per-direction tables + walk (J)",
+                   "l2": "inputs larger than L2 (elements, tree and alpha tables > 129 MB, "
+                         "rebuilt every step)",
+                   "parallelism": f"replicas x{world}"},
+        "walk_ms": walk_avg, "walk_units_per_s": world * units / (walk_avg * 1e-3),
+        "build_ms": ms_step - walk_avg,
+        "adjoint_forward_ratio": None,
+        "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--reference-sample", type=int, default=2048)
+    args = ap.parse_args()
+    world, rank, local = _dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

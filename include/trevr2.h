@@ -1,0 +1,185 @@
+/*
+ * trevr2.h — C ABI of the GB300 TREVR2 reverse-ray-trace library.
+ *
+ * The method is TREVR2 (Wadsley, Baumschlager & Shen, arXiv:2310.15235):
+ * for every active receiving element, rays leave along the HEALPix beam
+ * directions (Sec. 1.3, Sec. 2.5) through a binary radiation tree (Sec. 2.3),
+ * accumulating optical depth from cells whose absorption is the
+ * transmission average of their halves (Sec. 2.6, Eq. transmissionavg),
+ * and adding every source cell accepted by the opening criterion B/d > theta
+ * (Sec. 2.5.2), attenuated by e^{-tau} with tau taken along its beam to the
+ * projected distance and scaled by r/s (Sec. 2.5.1).  The result is the
+ * integrated intensity J = integral of I over solid angle, per receiver and
+ * band, whose far-field kernel is L/(4 pi r^2) (Eq. intint).
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers unless marked "host", contiguous,
+ *    row-major, in the units of the caller (positions in any length unit;
+ *    J comes back in luminosity per length^2).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  All work
+ *    is stream ordered; inputs may be released once the stream has passed
+ *    the call.
+ *  - The return value is TREVR2_OK (0) or a negative TREVR2_E* code; the
+ *    message of the last error on the calling thread is trevr2_last_error().
+ *    No C++ exception crosses this boundary and no kernel traps: device-side
+ *    problems are recorded in a status word and reported as error codes.
+ *  - Calls that use one tree must not overlap on the GPU (one stream, or
+ *    ordered by events): the tree owns one set of walk buffers.
+ */
+#ifndef TREVR2_H
+#define TREVR2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define TREVR2_OK 0
+#define TREVR2_EINVAL (-1)      /* invalid argument or input value            */
+#define TREVR2_ENOMEM (-2)      /* device or host allocation failed           */
+#define TREVR2_ECUDA (-3)       /* a CUDA runtime call failed                 */
+#define TREVR2_ETIMEOUT (-4)    /* a bounded device wait gave up              */
+#define TREVR2_EUNSUPPORTED (-5)/* outside the supported sizes (see below)    */
+#define TREVR2_EINTERNAL (-6)   /* an internal capacity check failed          */
+
+/* Flags of trevr2_J. */
+#define TREVR2_SOFT 1u   /* finite-size element kernel, Eq. intint (Sec. 2.2)   */
+#define TREVR2_THICK 2u  /* optically thick element factor, Eq. taucorr (Sec. 2.1) */
+#define TREVR2_ASYNC 4u  /* do not synchronise; check later with trevr2_status */
+
+/* Supported sizes: 1 <= nb <= 4 bands; nside a power of two in [1, 16];
+ * N < 2^31 elements; 1 <= bucket <= 4096. */
+#define TREVR2_MAX_BANDS 4
+#define TREVR2_MAX_NSIDE 16
+
+typedef struct trevr2_tree trevr2_tree;
+
+/*
+ * trevr2_build — the radiation tree of Sec. 2.3 with the per-cell
+ * quantities of Sec. 2.6 and Fig. sourcecombine (summed luminosity per band,
+ * centre of luminosity, bucket absorption sum(kappa m)/V_box).
+ *
+ *  pos     [N][3] float64  element positions
+ *  mass    [N]    float32  element masses (0 for pure point sources)
+ *  kappa   [N][nb] float32 opacity per unit mass, per band
+ *  lum     [N][nb] float32 luminosity per band
+ *  h       [N]    float32  element size (m/rho)^(1/3), used by TREVR2_SOFT and
+ *                          TREVR2_THICK; NULL = (V_root / N_gas)^(1/3)
+ *  N, nb   element and band counts (1 <= nb <= TREVR2_MAX_BANDS)
+ *  box_lo  host [3] lower corner of the root cube and box_size its edge;
+ *          box_lo == NULL or box_size <= 0 picks the bounding cube of the
+ *          positions (lo = per-axis minimum, edge = largest extent).  With an
+ *          explicit cube every position must lie inside it.
+ *  bucket  largest element count of a leaf (paper default 12)
+ *  out     receives the new tree; the tree owns its device memory until
+ *          trevr2_free.  The tree is geometric cyclic x,y,z bisection of
+ *          63-bit Morton keys; nodes are numbered breadth first, by key prefix
+ *          within a depth.
+ * Errors: EINVAL for NULL pointers, N < 0, nb out of range, non-finite
+ * positions, negative or non-finite mass/kappa/lum/h, positions outside an
+ * explicit cube; ENOMEM; ECUDA.  This call synchronises `stream`.
+ */
+int trevr2_build(const double* pos, const float* mass, const float* kappa, const float* lum,
+                 const float* h, int64_t N, int nb, const double* box_lo, double box_size,
+                 int bucket, void* stream, trevr2_tree** out);
+
+/*
+ * trevr2_J — integrated intensity J per active receiver and band
+ * (Sec. 2.5: cell opening B/d > theta, HEALPix beams with N_ray = 12 nside^2,
+ * transmission-averaged optical depth to each source's projected distance
+ * corrected by r/s, no self-illumination).
+ *
+ *  active  [A] int64  receiver indices in the caller's element order
+ *  nside   HEALPix resolution (power of two, 1..TREVR2_MAX_NSIDE); the alpha
+ *          tables for a new nside are built on first use and cached
+ *  theta   opening parameter theta_rad > 0 (paper default 0.75)
+ *  bands   host [nbsel] band indices to return, or NULL = all nb bands
+ *  flags   TREVR2_SOFT | TREVR2_THICK | TREVR2_ASYNC
+ *  J       [A][nbsel] float32 output, overwritten
+ * Active indices outside [0, N) give EINVAL (their rows are set to NaN).
+ * Without TREVR2_ASYNC the call synchronises `stream` and returns any device
+ * status; with it the call returns after enqueueing and trevr2_status
+ * reports the device status later.
+ */
+int trevr2_J(trevr2_tree* tree, const int64_t* active, int64_t A, int nside, float theta,
+             const int* bands, int nbsel, uint32_t flags, float* J, void* stream);
+
+/*
+ * trevr2_prepare — builds and caches the per-direction absorption tables of
+ * Eq. transmissionavg (Sec. 2.6; N_ray/2 values per cell and band) and the
+ * HEALPix beam table for `nside`, without running a walk.  trevr2_J does the
+ * same on first use of an nside; calling this first keeps that work out of
+ * a later trevr2_J.  Stream ordered, does not synchronise.
+ * Errors: EINVAL (NULL tree, bad nside), ENOMEM, ECUDA.
+ */
+int trevr2_prepare(trevr2_tree* tree, int nside, void* stream);
+
+/* Synchronises `stream` and returns (and clears) the tree's device status. */
+int trevr2_status(trevr2_tree* tree, void* stream);
+
+/* Releases the tree (stream ordered on the last stream the tree was used on). */
+int trevr2_free(trevr2_tree* tree);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* trevr2_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (a host-side count of launch calls, for accounting in benchmarks). */
+uint64_t trevr2_kernel_launches(void);
+
+/* ---- Introspection (tests and tools) --------------------------------- */
+
+typedef struct trevr2_tree_info {
+  int64_t n_elements;
+  int64_t n_nodes;
+  int64_t n_internal;
+  int64_t n_leaves;
+  int32_t nb;
+  int32_t bucket;
+  int32_t max_depth;
+  int32_t reserved;
+  double box_lo[3];
+  double box_size;
+} trevr2_tree_info;
+
+/* Host copy of the tree's sizes and root cube. */
+int trevr2_tree_info_get(const trevr2_tree* tree, trevr2_tree_info* info);
+
+/* Fields for trevr2_tree_export (element fields in sorted order, node fields
+ * in node order). */
+#define TREVR2_F_KEYS 1        /* uint64 [N] sorted Morton keys                  */
+#define TREVR2_F_PERM 2        /* int32  [N] sorted position -> caller index     */
+#define TREVR2_F_PREFIX 3      /* uint64 [n] node key prefix                     */
+#define TREVR2_F_DEPTH 4       /* int32  [n] node depth                          */
+#define TREVR2_F_FIRST 5       /* int32  [n] first element (sorted position)     */
+#define TREVR2_F_COUNT 6       /* int32  [n] element count                       */
+#define TREVR2_F_CHILD 7       /* int32  [n] lower child (upper = +1), -1 leaf   */
+#define TREVR2_F_PARENT 8      /* int32  [n] parent, -1 for the root             */
+#define TREVR2_F_LUM 9         /* float32 [n][nb] summed luminosity             */
+#define TREVR2_F_CENTRE 10     /* float64 [n][3] centre of luminosity (caller units) */
+#define TREVR2_F_ALPHA_LEAF 11 /* float32 [n][nb] bucket absorption (caller units), 0 internal */
+#define TREVR2_F_B 12          /* float64 [n] largest centre-to-corner distance (caller units) */
+
+/* Copies one field into `dst` (device, at least `bytes` bytes). */
+int trevr2_tree_export(const trevr2_tree* tree, int field, void* dst, size_t bytes, void* stream);
+
+/* Per-direction absorption of every node for one nside, as float32
+ * [n_nodes][6 nside^2][nb] in caller units (leaves repeat their isotropic
+ * value); builds and caches the tables if needed. */
+int trevr2_alpha_table(trevr2_tree* tree, int nside, float* dst, size_t bytes, void* stream);
+
+/* HEALPix RING pixel centres, float64 [12 nside^2][3] (Gorski et al. 2005). */
+int trevr2_healpix_pix2vec(int nside, double* dst, void* stream);
+
+/* HEALPix RING pixel of each of n direction vectors (float64 [n][3]),
+ * int32 [n] (Gorski et al. 2005). */
+int trevr2_healpix_vec2pix(int nside, const double* v, int64_t n, int32_t* pix, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TREVR2_H */

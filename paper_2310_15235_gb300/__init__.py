@@ -1,0 +1,278 @@
+"""GB300-native TREVR2 reverse ray trace (Wadsley, Baumschlager & Shen,
+arXiv:2310.15235): Python binding of the C ABI in ``include/trevr2.h``.
+
+This module only marshals arguments: every step of the method runs in the
+CUDA kernels of ``libtrevr2.so`` (built in-tree by ``build_lib.build()``).
+There is no CPU fallback; without the library every call raises.
+
+    tree = build(pos, mass, kappa, lum, h=None)    # Sec. 2.3 / 2.6
+    J = tree.J(active, nside=2, theta=0.75)        # Sec. 2.5, [A, nb] float32
+
+Tensors may live on the GPU (used in place) or on the host (copied to the
+current CUDA device first; the result stays on the device).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+
+import numpy as np
+import torch
+
+__all__ = [
+    "SOFT", "THICK", "ASYNC", "Tree", "TrevrError", "build", "J", "library_path", "load_library",
+    "healpix_pix2vec", "healpix_vec2pix", "exported_symbols", "FIELDS", "kernel_launches",
+]
+
+SOFT = 1
+THICK = 2
+ASYNC = 4
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libtrevr2.so")
+_HEADER = os.path.join(os.path.dirname(_HERE), "include", "trevr2.h")
+_lock = threading.Lock()
+_lib = None
+
+_CODES = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EUNSUPPORTED",
+          -6: "EINTERNAL"}
+
+FIELDS = {
+    "keys": (1, torch.int64, None), "perm": (2, torch.int32, None),
+    "prefix": (3, torch.int64, None), "depth": (4, torch.int32, None),
+    "first": (5, torch.int32, None), "count": (6, torch.int32, None),
+    "child": (7, torch.int32, None), "parent": (8, torch.int32, None),
+    "lum": (9, torch.float32, "nb"), "centre": (10, torch.float64, 3),
+    "alpha_leaf": (11, torch.float32, "nb"), "B": (12, torch.float64, None),
+}
+_NODE_FIELDS = {"prefix", "depth", "first", "count", "child", "parent", "lum", "centre",
+                "alpha_leaf", "B"}
+
+
+class TrevrError(RuntimeError):
+    """A negative status from libtrevr2 (the code name and the library's message)."""
+
+    def __init__(self, code: int, message: str):
+        self.code = code
+        super().__init__(f"{_CODES.get(code, code)}: {message}")
+
+
+class _Info(C.Structure):
+    _fields_ = [("n_elements", C.c_int64), ("n_nodes", C.c_int64), ("n_internal", C.c_int64),
+                ("n_leaves", C.c_int64), ("nb", C.c_int32), ("bucket", C.c_int32),
+                ("max_depth", C.c_int32), ("reserved", C.c_int32),
+                ("box_lo", C.c_double * 3), ("box_size", C.c_double)]
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libtrevr2 in this process so far."""
+    return int(load_library().trevr2_kernel_launches())
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def exported_symbols() -> list[str]:
+    """Entry points declared in include/trevr2.h."""
+    with open(_HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"\b(trevr2_[A-Za-z0-9_]+)\s*\(", text)))
+
+
+def load_library():
+    """Loads libtrevr2.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(
+                f"{_LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; "
+                f"g.build()\"` (nvcc, sm_103a); there is no CPU fallback")
+        lib = C.CDLL(_LIB_PATH)
+        P, i64, i32, f32, f64, u32, sz = (C.c_void_p, C.c_int64, C.c_int, C.c_float, C.c_double,
+                                          C.c_uint32, C.c_size_t)
+        lib.trevr2_build.argtypes = [P, P, P, P, P, i64, i32, P, f64, i32, P, C.POINTER(P)]
+        lib.trevr2_J.argtypes = [P, P, i64, i32, f32, P, i32, u32, P, P]
+        lib.trevr2_status.argtypes = [P, P]
+        lib.trevr2_prepare.argtypes = [P, i32, P]
+        lib.trevr2_free.argtypes = [P]
+        lib.trevr2_last_error.restype = C.c_char_p
+        lib.trevr2_tree_info_get.argtypes = [P, C.POINTER(_Info)]
+        lib.trevr2_tree_export.argtypes = [P, i32, P, sz, P]
+        lib.trevr2_alpha_table.argtypes = [P, i32, P, sz, P]
+        lib.trevr2_healpix_pix2vec.argtypes = [i32, P, P]
+        lib.trevr2_healpix_vec2pix.argtypes = [i32, P, i64, P, P]
+        for name in exported_symbols():
+            fn = getattr(lib, name)
+            if name not in ("trevr2_last_error", "trevr2_kernel_launches"):
+                fn.restype = C.c_int
+        lib.trevr2_kernel_launches.restype = C.c_uint64
+        lib.trevr2_kernel_launches.argtypes = []
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        msg = load_library().trevr2_last_error().decode(errors="replace")
+        raise TrevrError(rc, msg)
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev(x, dtype, device, shape=None):
+    """The argument as a contiguous CUDA tensor of `dtype` (copied if needed)."""
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.ascontiguousarray(x))
+    if not isinstance(x, torch.Tensor):
+        x = torch.as_tensor(x)
+    if x.dtype != dtype:
+        x = x.to(dtype)
+    if not x.is_cuda:
+        x = x.pin_memory().to(device, non_blocking=True) if x.numel() else x.to(device)
+    x = x.contiguous()
+    if shape is not None:
+        x = x.reshape(shape)
+    return x
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None and t.numel() else None
+
+
+class Tree:
+    """A radiation tree on the GPU (owns its device memory until `free`)."""
+
+    def __init__(self, handle, device):
+        self._h = handle
+        self.device = device
+        info = _Info()
+        _check(load_library().trevr2_tree_info_get(self._h, C.byref(info)))
+        self.N = int(info.n_elements)
+        self.nb = int(info.nb)
+        self.n_nodes = int(info.n_nodes)
+        self.n_internal = int(info.n_internal)
+        self.n_leaves = int(info.n_leaves)
+        self.max_depth = int(info.max_depth)
+        self.bucket = int(info.bucket)
+        self.box_lo = tuple(info.box_lo)
+        self.box_size = float(info.box_size)
+
+    # -- compute -------------------------------------------------------------
+    def J(self, active, nside: int = 2, theta: float = 0.75, bands=None, flags: int = 0,
+          out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Integrated intensity per active receiver and band, [A, nbsel] float32."""
+        self._alive()
+        act = _dev(active, torch.int64, self.device).reshape(-1)
+        nbsel = self.nb if bands is None else len(bands)
+        if out is None:
+            out = torch.empty((act.numel(), nbsel), dtype=torch.float32, device=self.device)
+        barr = None
+        if bands is not None:
+            barr = (C.c_int * len(bands))(*[int(b) for b in bands])
+        _check(load_library().trevr2_J(self._h, _ptr(act), act.numel(), int(nside), float(theta),
+                                       barr, int(nbsel), int(flags), _ptr(out),
+                                       _stream_ptr(stream)))
+        return out
+
+    def prepare(self, nside: int, stream=None):
+        """Builds and caches the per-direction tables for `nside` (no walk)."""
+        self._alive()
+        _check(load_library().trevr2_prepare(self._h, int(nside), _stream_ptr(stream)))
+
+    def status(self, stream=None):
+        self._alive()
+        _check(load_library().trevr2_status(self._h, _stream_ptr(stream)))
+
+    # -- introspection --------------------------------------------------------
+    def export(self, field: str) -> torch.Tensor:
+        self._alive()
+        code, dtype, cols = FIELDS[field]
+        rows = self.n_nodes if field in _NODE_FIELDS else self.N
+        shape = (rows,) if cols is None else (rows, self.nb if cols == "nb" else cols)
+        out = torch.empty(shape, dtype=dtype, device=self.device)
+        _check(load_library().trevr2_tree_export(self._h, code, _ptr(out),
+                                                 out.numel() * out.element_size(),
+                                                 _stream_ptr()))
+        torch.cuda.current_stream().synchronize()
+        return out
+
+    def alpha_table(self, nside: int) -> torch.Tensor:
+        self._alive()
+        out = torch.empty((self.n_nodes, 6 * nside * nside, self.nb), dtype=torch.float32,
+                          device=self.device)
+        _check(load_library().trevr2_alpha_table(self._h, int(nside), _ptr(out),
+                                                 out.numel() * 4, _stream_ptr()))
+        torch.cuda.current_stream().synchronize()
+        return out
+
+    # -- lifetime -------------------------------------------------------------
+    def _alive(self):
+        if not self._h:
+            raise ValueError("tree already freed")
+
+    def free(self):
+        if getattr(self, "_h", None):
+            load_library().trevr2_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build(pos, mass, kappa, lum, h=None, box_lo=None, box_size: float = 0.0, bucket: int = 12,
+          device=None, stream=None) -> Tree:
+    """Builds the radiation tree (Sec. 2.3) from element positions [N,3] (float64),
+    masses [N], opacities [N,nb], luminosities [N,nb] and optional sizes h [N]."""
+    lib = load_library()
+    if device is None:
+        device = pos.device if isinstance(pos, torch.Tensor) and pos.is_cuda else torch.device(
+            "cuda", torch.cuda.current_device())
+    p = _dev(pos, torch.float64, device)
+    n = p.numel() // 3
+    p = p.reshape(n, 3)
+    m = _dev(mass, torch.float32, device).reshape(n)
+    k = _dev(kappa, torch.float32, device).reshape(n, -1)
+    nb = k.shape[1] if n else (k.shape[1] if k.dim() == 2 else 1)
+    l_ = _dev(lum, torch.float32, device).reshape(n, nb)
+    hh = None if h is None else _dev(h, torch.float32, device).reshape(n)
+    lo = None
+    if box_lo is not None and box_size > 0:
+        lo = (C.c_double * 3)(*[float(v) for v in box_lo])
+    handle = C.c_void_p()
+    with torch.cuda.device(device):
+        _check(lib.trevr2_build(_ptr(p), _ptr(m), _ptr(k), _ptr(l_), _ptr(hh), n, int(nb), lo,
+                                float(box_size if lo is not None else 0.0), int(bucket),
+                                _stream_ptr(stream), C.byref(handle)))
+    return Tree(handle, device)
+
+
+def J(tree: Tree, active, nside: int = 2, theta: float = 0.75, bands=None, flags: int = 0,
+      out=None, stream=None) -> torch.Tensor:
+    return tree.J(active, nside, theta, bands, flags, out, stream)
+
+
+def healpix_pix2vec(nside: int, device=None) -> torch.Tensor:
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    out = torch.empty((12 * nside * nside, 3), dtype=torch.float64, device=device)
+    _check(load_library().trevr2_healpix_pix2vec(int(nside), _ptr(out), _stream_ptr()))
+    return out
+
+
+def healpix_vec2pix(nside: int, v) -> torch.Tensor:
+    v = _dev(v, torch.float64, torch.device("cuda", torch.cuda.current_device())).reshape(-1, 3)
+    out = torch.empty((v.shape[0],), dtype=torch.int32, device=v.device)
+    _check(load_library().trevr2_healpix_vec2pix(int(nside), _ptr(v), v.shape[0], _ptr(out),
+                                                 _stream_ptr()))
+    return out

@@ -1,0 +1,66 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for
+sm_103a, loads, and exports every entry point the header declares."""
+
+import ctypes
+import subprocess
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2310_15235_gb300 import build_lib
+    build_lib.build()
+    import paper_2310_15235_gb300 as t2
+    return t2
+
+
+def test_header_declares_the_boundary(lib):
+    syms = lib.exported_symbols()
+    for name in ("trevr2_build", "trevr2_J", "trevr2_free", "trevr2_last_error", "trevr2_status",
+                 "trevr2_tree_info_get", "trevr2_tree_export", "trevr2_alpha_table",
+                 "trevr2_healpix_pix2vec", "trevr2_healpix_vec2pix"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = ctypes.CDLL(lib.library_path())
+    missing = [s for s in lib.exported_symbols() if not hasattr(so, s)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.library_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert set(lib.exported_symbols()) <= exported
+
+
+def test_library_targets_sm103a(lib):
+    out = subprocess.run(["cuobjdump", "--list-elf", lib.library_path()], capture_output=True,
+                         text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_last_error_without_gpu_work(lib):
+    so = lib.load_library()
+    # argument validation happens on the host before any CUDA call
+    rc = so.trevr2_build(None, None, None, None, None, -1, 1, None, 0.0, 12, None, None)
+    assert rc == -1
+    assert b"out is NULL" in so.trevr2_last_error()
+    handle = ctypes.c_void_p()
+    rc = so.trevr2_build(None, None, None, None, None, 10, 1, None, 0.0, 12, None,
+                         ctypes.byref(handle))
+    assert rc == -1 and b"NULL input" in so.trevr2_last_error()
+    rc = so.trevr2_build(None, None, None, None, None, 0, 9, None, 0.0, 12, None,
+                         ctypes.byref(handle))
+    assert rc == -5
+    assert so.trevr2_J(None, None, 0, 2, ctypes.c_float(0.75), None, 0, 0, None, None) == -1
+    assert so.trevr2_free(None) == 0
+
+
+def test_python_layer_fails_loudly_without_library(monkeypatch, tmp_path):
+    import paper_2310_15235_gb300 as t2
+    monkeypatch.setattr(t2, "_LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(t2, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        t2.load_library()
