@@ -117,6 +117,31 @@ int trevr2_J(trevr2_tree* tree, const int64_t* active, int64_t A, int nside, flo
  */
 int trevr2_prepare(trevr2_tree* tree, int nside, void* stream);
 
+/*
+ * trevr2_J_noalloc — trevr2_J without any device allocation.  The paper has
+ * no counterpart: this entry point exists for callers that cannot let a
+ * library allocate device memory (host codes that own all device memory
+ * through their own arena or a fixed budget, or that call from a context
+ * where an allocation could block or fail).
+ *
+ * Arguments, output and errors are those of trevr2_J, with two differences:
+ *  - the tables for `nside` must already exist (trevr2_prepare, or an
+ *    earlier trevr2_J with the same nside); otherwise EINVAL;
+ *  - the walk buffers live in one fixed 16 MiB device array inside the
+ *    library (256 source records per warp and pass, which caps the grid at
+ *    1,816 resident warps).  The walk loops over receivers and makes more
+ *    passes when a receiver has more sources, so any A works; a launch that
+ *    would need more than the array holds is rejected with EUNSUPPORTED.
+ * Every process that loads the library holds that array on each GPU it uses
+ * until it exits.  All calls share the array: calls whose work overlaps on
+ * the GPU (on any tree, from any thread or stream) race and must be ordered
+ * by the caller.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.
+ */
+int trevr2_J_noalloc(trevr2_tree* tree, const int64_t* active, int64_t A, int nside, float theta,
+                     const int* bands, int nbsel, uint32_t flags, float* J, void* stream);
+
 /* Synchronises `stream` and returns (and clears) the tree's device status. */
 int trevr2_status(trevr2_tree* tree, void* stream);
 

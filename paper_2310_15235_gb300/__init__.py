@@ -100,6 +100,7 @@ def load_library():
         lib.trevr2_J.argtypes = [P, P, i64, i32, f32, P, i32, u32, P, P]
         lib.trevr2_status.argtypes = [P, P]
         lib.trevr2_prepare.argtypes = [P, i32, P]
+        lib.trevr2_J_noalloc.argtypes = [P, P, i64, i32, f32, P, i32, u32, P, P]
         lib.trevr2_free.argtypes = [P]
         lib.trevr2_last_error.restype = C.c_char_p
         lib.trevr2_tree_info_get.argtypes = [P, C.POINTER(_Info)]

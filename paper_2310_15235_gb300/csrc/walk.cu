@@ -670,3 +670,193 @@ extern "C" int trevr2_prepare(trevr2_tree* tree, int nside, void* stream) {
   Table* tb = nullptr;
   return ensure_table(t, nside, st, &tb);
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of trevr2_J.
+//
+// Some host codes cannot let a library call cudaMalloc: they own every byte
+// of device memory through their own arena or a fixed memory budget, or they
+// call in from a context where a device allocation could block or fail.  For
+// them the walk buffers come from one file-scope device array of fixed size
+// instead of the tree's grown-on-demand buffers.  Every process that loads
+// this library holds the array on every GPU it uses until it exits.
+#include <mutex>
+
+namespace trevr2 {
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB per device
+constexpr int kNoAllocSources = 256;  // source records per warp and pass
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the array for the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+static int noalloc_scratch(void** out) {
+  int dev = 0;
+  T2_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_error("trevr2_J_noalloc: device ordinal %d above %d", dev, kNoAllocMaxDevices - 1);
+    return TREVR2_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(walk scratch)");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return TREVR2_OK;
+}
+
+static int launch_walk_noalloc(Tree* t, Table* tb, const int64_t* active, int64_t A, int nside,
+                               float theta, const int* bsel, int nbsel, uint32_t flags, float* J,
+                               cudaStream_t st) {
+  void* scratch = nullptr;
+  T2_CHECK(noalloc_scratch(&scratch));
+  int dev = 0, sms = 0;
+  T2_CUDA(cudaGetDevice(&dev));
+  T2_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  WalkArgs a;
+  a.nodes = t->nodes;
+  a.csrc = t->csrc;
+  a.c64 = t->c64;
+  a.B64 = t->B64;
+  a.Lnode = t->Lnode;
+  a.alpha_leaf = t->alpha_leaf;
+  a.alpha_tab = tb->alpha;
+  a.pos32 = t->pos32;
+  a.pos64 = t->pos64;
+  a.Lelem = t->Lelem;
+  a.inv = t->inv;
+  a.hn = t->hn;
+  a.km = t->km;
+  a.dirs = tb->dirs;
+  a.active = active;
+  a.A = A;
+  a.N = t->N;
+  a.nside = nside;
+  a.npix = 12 * nside * nside;
+  a.P = a.npix / 2;
+  a.theta = theta;
+  a.theta2 = theta * theta;
+  a.theta64 = double(theta);
+  a.guard_abs = 2e-7f * theta + 2e-7f;
+  a.guard_rel = 2e-6f;
+  a.flags = flags;
+  a.nb = t->nb;
+  a.nbsel = nbsel;
+  for (int b = 0; b < TREVR2_MAX_BANDS; ++b) a.bsel[b] = b < nbsel ? bsel[b] : 0;
+  a.inv_size2 = 1.0 / (t->size * t->size);
+  a.size = t->size;
+  a.J = J;
+  a.M = kNoAllocSources;
+  a.max_depth = t->max_depth;
+  a.stack_ints = 64 * (t->max_depth + 2);
+  a.status = t->status;
+  a.counter = t->counter;
+  const size_t smem = size_t(kWalkWarps) * (a.stack_ints + a.npix + 1) * sizeof(int);
+  int max_smem = 0;
+  T2_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (smem > size_t(max_smem)) {
+    set_error("trevr2_J_noalloc: tree depth %d with nside %d needs %zu bytes of shared memory",
+              t->max_depth, nside, smem);
+    return TREVR2_EUNSUPPORTED;
+  }
+  const void* fn = t->nbp == 1 ? reinterpret_cast<const void*>(&k_walk<1>)
+                 : t->nbp == 2 ? reinterpret_cast<const void*>(&k_walk<2>)
+                               : reinterpret_cast<const void*>(&k_walk<4>);
+  T2_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  int per_sm = 0;
+  T2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kWalkWarps * 32, smem));
+  if (per_sm < 1) per_sm = 1;
+  // The grid is capped by what the fixed array holds; the kernel loops over
+  // receivers and passes over sources, so any A and any source count fit.
+  const size_t per_block = size_t(kWalkWarps) * a.M * (2 * sizeof(SrcEntry) + sizeof(int));
+  const int64_t max_blocks = int64_t(kNoAllocScratchBytes / per_block);
+  if (max_blocks < 1) {
+    set_error("trevr2_J_noalloc: one block needs %zu bytes of walk buffers, the fixed array "
+              "holds %zu", per_block, kNoAllocScratchBytes);
+    return TREVR2_EUNSUPPORTED;
+  }
+  int64_t blocks = int64_t(sms) * per_sm;
+  blocks = std::min<int64_t>(blocks, (A + kWalkWarps - 1) / kWalkWarps);
+  blocks = std::min<int64_t>(blocks, max_blocks);
+  blocks = std::max<int64_t>(blocks, 1);
+  const size_t warps = size_t(blocks) * kWalkWarps;
+  char* base = static_cast<char*>(scratch);
+  a.srcU = reinterpret_cast<SrcEntry*>(base);
+  a.srcV = reinterpret_cast<SrcEntry*>(base + warps * a.M * sizeof(SrcEntry));
+  a.pixU = reinterpret_cast<int*>(base + 2 * warps * a.M * sizeof(SrcEntry));
+  T2_CUDA(cudaMemsetAsync(t->counter, 0, sizeof(unsigned long long), st));
+  void* args[] = {&a};
+  T2_CUDA(cudaLaunchKernel(fn, dim3(unsigned(blocks)), dim3(kWalkWarps * 32), args, smem, st));
+  note_launch();
+  return TREVR2_OK;
+}
+
+}  // namespace trevr2
+
+extern "C" int trevr2_J_noalloc(trevr2_tree* tree, const int64_t* active, int64_t A, int nside,
+                                float theta, const int* bands, int nbsel, uint32_t flags,
+                                float* J, void* stream) {
+  clear_error();
+  if (!tree) {
+    set_error("trevr2_J_noalloc: tree is NULL");
+    return TREVR2_EINVAL;
+  }
+  Tree* t = reinterpret_cast<Tree*>(tree);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  t->last_stream = st;
+  if (A < 0 || (A > 0 && (!active || !J))) {
+    set_error("trevr2_J_noalloc: A < 0 or NULL active/J");
+    return TREVR2_EINVAL;
+  }
+  if (!valid_nside(nside)) {
+    set_error("trevr2_J_noalloc: nside %d is not a power of two in [1, %d]", nside,
+              TREVR2_MAX_NSIDE);
+    return nside > TREVR2_MAX_NSIDE ? TREVR2_EUNSUPPORTED : TREVR2_EINVAL;
+  }
+  if (!(theta > 0.0f) || !std::isfinite(theta)) {
+    set_error("trevr2_J_noalloc: theta must be positive and finite");
+    return TREVR2_EINVAL;
+  }
+  if (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_ASYNC)) {
+    set_error("trevr2_J_noalloc: unknown flag bits 0x%x", flags);
+    return TREVR2_EINVAL;
+  }
+  int bsel[TREVR2_MAX_BANDS];
+  if (bands) {
+    if (nbsel < 1 || nbsel > t->nb) {
+      set_error("trevr2_J_noalloc: nbsel = %d outside [1, %d]", nbsel, t->nb);
+      return TREVR2_EINVAL;
+    }
+    for (int b = 0; b < nbsel; ++b) {
+      if (bands[b] < 0 || bands[b] >= t->nb) {
+        set_error("trevr2_J_noalloc: band index %d outside [0, %d)", bands[b], t->nb);
+        return TREVR2_EINVAL;
+      }
+      bsel[b] = bands[b];
+    }
+  } else {
+    nbsel = t->nb;
+    for (int b = 0; b < nbsel; ++b) bsel[b] = b;
+  }
+  if (A == 0) return TREVR2_OK;
+  Table* tb = nullptr;
+  for (Table& cand : t->tables)
+    if (cand.nside == nside) tb = &cand;
+  if (!tb) {
+    set_error("trevr2_J_noalloc: no tables for nside %d; call trevr2_prepare(tree, %d) first "
+              "(this entry point never allocates)", nside, nside);
+    return TREVR2_EINVAL;
+  }
+  T2_CHECK(launch_walk_noalloc(t, tb, active, A, nside, theta, bsel, nbsel, flags, J, st));
+  if (flags & TREVR2_ASYNC) return TREVR2_OK;
+  return read_status(t, st);
+}
