@@ -331,6 +331,41 @@ def run_ours(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_walk_only(args):
+    """The walk kernel alone on a clumpy field of lattice^3 gas (profiling
+    aid): tree and tables built once, then `warmup + steps` walks."""
+    import torch
+
+    import paper_2310_15235_gb300 as t2
+
+    dev = torch.device("cuda", 0)
+    n = args.lattice
+    case = workloads._clumpy(1003, n, 1.5, max(1, 10_000 * n ** 3 // 128 ** 3), [10.0, 3.0, 0.5],
+                             4, 0.5, f"clumpy_multiband_{n}")
+    inp = {k: torch.from_numpy(np.ascontiguousarray(case[k])).to(dev)
+           for k in ("pos", "mass", "kappa", "lum", "h", "active")}
+    tree = t2.build(inp["pos"], inp["mass"], inp["kappa"], inp["lum"], inp["h"], case["box_lo"],
+                    case["box_size"], case["bucket"], device=dev)
+    tree.prepare(case["nside"])
+    A, nb, npix = len(case["active"]), case["nb"], 12 * case["nside"] ** 2
+    J = torch.empty((A, nb), dtype=torch.float32, device=dev)
+    times = []
+    for k in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tree.J(inp["active"], case["nside"], case["theta"], out=J, flags=t2.ASYNC)
+        e1.record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    tree.status()
+    ms = float(np.mean(times))
+    print(json.dumps({"mode": "walk-only", "lattice": n, "receivers": A, "walk_ms": ms,
+                      "units_per_s": A * npix * nb / (ms * 1e-3), "nodes": tree.n_nodes,
+                      "max_depth": tree.max_depth}), flush=True)
+    tree.free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -340,7 +375,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--reference-sample", type=int, default=2048)
+    ap.add_argument("--walk-only", action="store_true",
+                    help="time only the walk kernel on a lattice^3 clumpy field (profiling)")
+    ap.add_argument("--lattice", type=int, default=128)
     args = ap.parse_args()
+    if args.walk_only:
+        run_walk_only(args)
+        return
     world, rank, local = _dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -185,8 +185,11 @@ __global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const int* __r
   }
 }
 
-int radix_sort_u64_i32(uint64_t* keys, int* vals, int64_t n, cudaStream_t st) {
+int radix_sort_u64_i32(uint64_t* keys, int* vals, int64_t n, cudaStream_t st, int key_bits) {
   if (n <= 1) return TREVR2_OK;
+  // an even number of 8-bit passes, so the result ends in the caller's buffers
+  int passes = (std::min(std::max(key_bits, 1), 64) + 7) / 8;
+  passes += passes & 1;
   const int ntiles = int((n + kSortTile - 1) / kSortTile);
   uint64_t* k2 = nullptr;
   int* v2 = nullptr;
@@ -196,14 +199,13 @@ int radix_sort_u64_i32(uint64_t* keys, int* vals, int64_t n, cudaStream_t st) {
   T2_CHECK(dalloc(&hist, size_t(256) * ntiles, st));
   uint64_t *ka = keys, *kb = k2;
   int *va = vals, *vb = v2;
-  for (int shift = 0; shift < 64; shift += 8) {
+  for (int shift = 0; shift < 8 * passes; shift += 8) {
     k_radix_hist<<<ntiles, kSortThreads, 0, st>>>(ka, n, shift, hist, ntiles); note_launch();
     T2_CHECK(scan_exclusive_i32(hist, int64_t(256) * ntiles, nullptr, st));
     k_radix_scatter<<<ntiles, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, hist, ntiles); note_launch();
     std::swap(ka, kb);
     std::swap(va, vb);
   }
-  // 8 passes: the result is back in the caller's buffers.
   dfree(k2, st);
   dfree(v2, st);
   dfree(hist, st);
@@ -468,7 +470,7 @@ __global__ void k_aggregate_level(int64_t lb, int64_t le, int nb, int nbp, doubl
   w.child = c;
   w.aux = c < 0 ? first[q] : int_index[q];
   w.count = count[q];
-  w.meta = uint32_t(d) | (c < 0 ? kMetaLeaf : 0u) | has;
+  w.meta = uint32_t(d) | (uint32_t(d % 3) << kMetaAxisShift) | (c < 0 ? kMetaLeaf : 0u) | has;
   nodes[q] = w;
 }
 
@@ -541,6 +543,8 @@ static void free_tree(Tree* t, cudaStream_t st) {
   t->tables.clear();
   if (t->scratch) cudaFreeAsync(t->scratch, st);
   t->scratch = nullptr;
+  if (t->order_buf) cudaFreeAsync(t->order_buf, st);
+  t->order_buf = nullptr;
   dfree(t->status, st);
   dfree(t->counter, st);
 }

@@ -32,6 +32,7 @@ constexpr uint32_t kMetaDepthMask = 63u;
 constexpr uint32_t kMetaLeaf = 1u << 8;
 constexpr uint32_t kMetaHasL = 1u << 9;      // some luminosity below
 constexpr uint32_t kMetaHasAlpha = 1u << 10; // some absorption below
+constexpr int kMetaAxisShift = 12;            // split axis (depth mod 3) in bits 12-13
 
 // Source found by the cut, binned to its beam: projected distance s along
 // the beam, r/s, the geometric kernel g(r), and where its luminosity lives.
@@ -113,6 +114,8 @@ struct Tree {
   // walk buffers (grown on demand)
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  void* order_buf = nullptr;   // receivers in key order: keys + slots
+  size_t order_bytes = 0;
   uint32_t* status = nullptr;             // device status word
   unsigned long long* counter = nullptr;  // device work counter
 };
@@ -159,8 +162,8 @@ void dfree(T*& p, cudaStream_t st) {
 // Exclusive scan of n int32 values in place; *d_total (device) gets the sum.
 int scan_exclusive_i32(int* d, int64_t n, int* d_total, cudaStream_t st);
 
-// Stable LSD radix sort of 63-bit keys with int32 payload (in place).
-int radix_sort_u64_i32(uint64_t* keys, int* vals, int64_t n, cudaStream_t st);
+// Stable LSD radix sort of keys below 2^key_bits with int32 payload (in place).
+int radix_sort_u64_i32(uint64_t* keys, int* vals, int64_t n, cudaStream_t st, int key_bits = 64);
 
 // Alpha tables and beam directions for one nside (built and cached).
 int ensure_table(Tree* t, int nside, cudaStream_t st, Table** out);

@@ -99,6 +99,24 @@ __device__ __noinline__ bool opens64(const WalkArgs& a, int q, const NodeW& nd, 
   return (d == 0.0) || (a.B64[q] > __dmul_rn(a.theta64, d));
 }
 
+// Coordinates for decisions on beams that lie in a plane of constant x[c]
+// (a zero beam component): half-open boxes [lo, hi) hold the beam iff
+// lo <= x[c] < hi, decided as on the FP64 position.  Box faces are
+// multiples of 2^-21, exact in FP32, and rounding to nearest never carries a
+// coordinate across one; the FP32 value only disagrees when it lands on a
+// face that the FP64 value lies just below, and then the next float below
+// restores the FP64 answer.
+__device__ __forceinline__ float3 grazing_coords(const WalkArgs& a, int si, float3 x) {
+  const double* p = a.pos64 + 3 * int64_t(si);
+  float g[3] = {x.x, x.y, x.z};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double f = double(g[c]) * 2097152.0;
+    if (f == floor(f) && p[c] < double(g[c])) g[c] = nextafterf(g[c], -INFINITY);
+  }
+  return make_float3(g[0], g[1], g[2]);
+}
+
 // Sec. 2.5.2: open iff d == 0 or B > theta d.
 __device__ __forceinline__ bool cell_opens(const WalkArgs& a, int q, const NodeW& nd, float3 x,
                                            int si) {
@@ -442,7 +460,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkArgs a) {
     }
     const int si = a.inv[io];
     const float4 xr = a.pos32[si];
-    const float3 x = make_float3(xr.x, xr.y, xr.z);
+    // the receiver in FP32, on the FP64 side of every box face
+    const float3 x = grazing_coords(a, si, make_float3(xr.x, xr.y, xr.z));
     float Js[NBP], Jc[NBP];
 #pragma unroll
     for (int b = 0; b < NBP; ++b) Js[b] = Jc[b] = 0.0f;

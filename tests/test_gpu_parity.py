@@ -278,3 +278,21 @@ def test_J_clumpy_2M_sampled(t2, oracle_mod, clumpy):
     ref = ot.J(case["active"][idx], case["nside"], case["theta"])
     _assert_J(J[idx], ref, "clumpy 2M sampled")
     tree.free()
+
+
+@pytest.mark.parametrize("nside", [1, 2, 4])
+def test_J_receivers_on_root_faces(t2, oracle_mod, nside):
+    """Receivers exactly on the faces of the root cube, seen along beams with
+    zero components (nside 1 and 2 have beams along the axes and in the
+    equatorial plane): half-open boxes decide which cells such beams cross."""
+    case = workloads.random_case(1200, 30, nb=2, seed=24, clumped=True, n_active=400)
+    rng = np.random.default_rng(5)
+    for i in rng.choice(1200, 60, replace=False):
+        case["pos"][i, rng.integers(0, 3)] = rng.choice([0.0, 1.0])
+    act = np.unique(np.concatenate([case["active"], np.flatnonzero(
+        ((case["pos"][:1200] == 0.0) | (case["pos"][:1200] == 1.0)).any(1))]))
+    tree = _gpu_tree(t2, case)
+    J = tree.J(act, nside, 0.75).cpu().numpy()
+    ref = oracle_mod.OracleTree.from_case(case).J(act, nside, 0.75)
+    _assert_J(J, ref, f"root faces nside={nside}")
+    tree.free()
