@@ -142,6 +142,107 @@ int trevr2_prepare(trevr2_tree* tree, int nside, void* stream);
 int trevr2_J_noalloc(trevr2_tree* tree, const int64_t* active, int64_t A, int nside, float theta,
                      const int* bands, int nbsel, uint32_t flags, float* J, void* stream);
 
+/*
+ * trevr2_J_backward — adjoint of trevr2_J: for a loss whose gradient with
+ * respect to J is gJ, returns dLoss/dkappa and dLoss/dlum of every element.
+ * It differentiates the same map as trevr2_J with the discrete choices held
+ * fixed (tree, cut of Sec. 2.5.2, beam of every source): through the
+ * attenuation e^{-tau} of every source along its beam (Sec. 2.5.1), the
+ * transmission average of the per-direction absorption (Sec. 2.6,
+ * Eq. transmissionavg) down to the bucket absorption sum(kappa m)/V_box of
+ * the leaves, the cell luminosities and their centres of luminosity, and,
+ * with TREVR2_THICK, the receiver's own Eq. taucorr factor.  The traversals
+ * are walked again; nothing from the forward call is kept.
+ *
+ *  active, A, nside, theta, bands, nbsel, flags   as for trevr2_J
+ *  gJ       [A][nbsel] float32 dLoss/dJ (rows and columns as trevr2_J's J)
+ *  g_kappa  [N][nb] float32 output dLoss/dkappa in the caller's element
+ *           order (the units of J per unit kappa), overwritten
+ *  g_lum    [N][nb] float32 output dLoss/dlum, overwritten
+ * Positions, masses and sizes are not differentiated.  The call allocates
+ * its gradient buffers (about the size of the alpha table for nside plus
+ * 8 nb floats per element) stream ordered and frees them before returning.
+ * Errors: as trevr2_J (EINVAL, EUNSUPPORTED, ENOMEM, ECUDA).  Without
+ * TREVR2_ASYNC the call synchronises `stream` and returns the device status.
+ */
+int trevr2_J_backward(trevr2_tree* tree, const int64_t* active, int64_t A, int nside, float theta,
+                      const int* bands, int nbsel, uint32_t flags, const float* gJ,
+                      float* g_kappa, float* g_lum, void* stream);
+
+/* ---- Batches: many receiver subsets over several trees -------------- */
+
+/*
+ * With individual timesteps (Sec. 1.2) only the elements on the current rung
+ * need J, so one step asks for many small receiver subsets; Sec. 3.1 runs
+ * several independent snapshots.  A batch walks all of them in one persistent
+ * launch: subsets s = 0..nsub-1 are concatenated, subset s owning rows
+ * offsets[s] <= r < offsets[s+1] of `active` and of J, and walked in tree
+ * trees[tree_of[s]].  Each row equals what trevr2_J gives for the same tree,
+ * receiver, nside, theta and flags (all nb bands, in band order).
+ */
+typedef struct trevr2_batch trevr2_batch;
+
+/* Most trees in one batch. */
+#define TREVR2_MAX_BATCH_TREES 32
+
+/*
+ * trevr2_batch_create — a reusable batch plan.
+ *  trees    host [ntrees] trees with the same band count nb
+ *           (1 <= ntrees <= TREVR2_MAX_BATCH_TREES); they must outlive the
+ *           plan and must not be rebuilt while it exists
+ *  offsets  host [nsub + 1] int64, offsets[0] = 0, non-decreasing
+ *  tree_of  host [nsub] int, tree index of each subset
+ *  nside, theta, flags   as for trevr2_J (TREVR2_ASYNC is ignored here)
+ *  out      receives the plan.  Creation builds any missing alpha tables of
+ *           the trees for `nside`, copies offsets/tree_of to the device and
+ *           allocates the walk buffers of the default launch shape.  It
+ *           synchronises `stream`.
+ * Errors: EINVAL (NULL arrays, mismatched band counts, bad offsets or
+ * tree_of, bad nside/theta/flags), EUNSUPPORTED (too many trees, nside > 16,
+ * shared memory exceeded by the deepest tree), ENOMEM, ECUDA.
+ */
+int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const int64_t* offsets,
+                        const int* tree_of, int nsub, int nside, float theta, uint32_t flags,
+                        void* stream, trevr2_batch** out);
+
+/*
+ * trevr2_batch_run — enqueues the whole batch: one memset of the work
+ * counter and one kernel launch, with no allocation and no synchronisation.
+ *  active  [offsets[nsub]] int64 receiver indices (each in its subset's tree)
+ *  J       [offsets[nsub]][nb] float32 output, overwritten
+ * Does not synchronise; trevr2_batch_status reports device errors (indices
+ * outside [0, N) give NaN rows and EINVAL there).  Runs of one plan must not
+ * overlap on the GPU (they share the plan's counter and buffers).
+ */
+int trevr2_batch_run(trevr2_batch* batch, const int64_t* active, float* J, void* stream);
+
+/*
+ * trevr2_batch_autotune — times every launch shape (4 or 8 warps per block
+ * x 512, 1024 or 2048 staged sources per warp and pass) on the first
+ * min(offsets[nsub], 65536) rows of `active`, keeps the fastest for later
+ * runs and re-sizes the buffers for it.  `J` is overwritten (its first rows).
+ * warps_out / staging_out (host, may be NULL) receive the chosen shape.
+ * Synchronises `stream`.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int trevr2_batch_autotune(trevr2_batch* batch, const int64_t* active, float* J, void* stream,
+                          int* warps_out, int* staging_out);
+
+/* Synchronises `stream`; returns (and clears) the device status of the
+ * batch's trees (the first error found). */
+int trevr2_batch_status(trevr2_batch* batch, void* stream);
+
+/* Releases the plan (not its trees), stream ordered on the last stream used. */
+int trevr2_batch_free(trevr2_batch* batch);
+
+/*
+ * trevr2_J_batched — one-shot convenience: create, run, status (unless
+ * TREVR2_ASYNC, in which case trevr2_status of each tree reports later) and
+ * free.  Arguments as for trevr2_batch_create and trevr2_batch_run.
+ */
+int trevr2_J_batched(trevr2_tree* const* trees, int ntrees, const int64_t* active,
+                     const int64_t* offsets, const int* tree_of, int nsub, int nside, float theta,
+                     uint32_t flags, float* J, void* stream);
+
 /* Synchronises `stream` and returns (and clears) the tree's device status. */
 int trevr2_status(trevr2_tree* tree, void* stream);
 

@@ -25,6 +25,7 @@ import torch
 __all__ = [
     "SOFT", "THICK", "ASYNC", "Tree", "TrevrError", "build", "J", "library_path", "load_library",
     "healpix_pix2vec", "healpix_vec2pix", "exported_symbols", "FIELDS", "kernel_launches",
+    "Batch", "J_batched", "J_fn",
 ]
 
 SOFT = 1
@@ -102,6 +103,13 @@ def load_library():
         lib.trevr2_prepare.argtypes = [P, i32, P]
         lib.trevr2_J_noalloc.argtypes = [P, P, i64, i32, f32, P, i32, u32, P, P]
         lib.trevr2_free.argtypes = [P]
+        lib.trevr2_batch_create.argtypes = [P, i32, P, P, i32, i32, f32, u32, P, C.POINTER(P)]
+        lib.trevr2_batch_run.argtypes = [P, P, P, P]
+        lib.trevr2_batch_autotune.argtypes = [P, P, P, P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        lib.trevr2_batch_status.argtypes = [P, P]
+        lib.trevr2_batch_free.argtypes = [P]
+        lib.trevr2_J_batched.argtypes = [P, i32, P, P, P, i32, i32, f32, u32, P, P]
+        lib.trevr2_J_backward.argtypes = [P, P, i64, i32, f32, P, i32, u32, P, P, P, P]
         lib.trevr2_last_error.restype = C.c_char_p
         lib.trevr2_tree_info_get.argtypes = [P, C.POINTER(_Info)]
         lib.trevr2_tree_export.argtypes = [P, i32, P, sz, P]
@@ -184,6 +192,24 @@ class Tree:
                                        _stream_ptr(stream)))
         return out
 
+    def J_backward(self, active, gJ, nside: int = 2, theta: float = 0.75, bands=None,
+                   flags: int = 0, stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+        """Adjoint of `J`: given gJ = dLoss/dJ [A, nbsel], returns
+        (dLoss/dkappa [N, nb], dLoss/dlum [N, nb]) in the caller's element order."""
+        self._alive()
+        act = _dev(active, torch.int64, self.device).reshape(-1)
+        nbsel = self.nb if bands is None else len(bands)
+        g = _dev(gJ, torch.float32, self.device).reshape(act.numel(), nbsel)
+        gk = torch.empty((self.N, self.nb), dtype=torch.float32, device=self.device)
+        gl = torch.empty((self.N, self.nb), dtype=torch.float32, device=self.device)
+        barr = None
+        if bands is not None:
+            barr = (C.c_int * len(bands))(*[int(b) for b in bands])
+        _check(load_library().trevr2_J_backward(self._h, _ptr(act), act.numel(), int(nside),
+                                                float(theta), barr, int(nbsel), int(flags),
+                                                _ptr(g), _ptr(gk), _ptr(gl), _stream_ptr(stream)))
+        return gk, gl
+
     def prepare(self, nside: int, stream=None):
         """Builds and caches the per-direction tables for `nside` (no walk)."""
         self._alive()
@@ -232,6 +258,112 @@ class Tree:
             pass
 
 
+def _subset_layout(trees, offsets, tree_of):
+    """Host arrays of a batch: tree handles, offsets [nsub+1] int64, tree_of [nsub] int32."""
+    trees = list(trees)
+    for t in trees:
+        t._alive()
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64).reshape(-1))
+    tof = np.ascontiguousarray(np.asarray(tree_of, dtype=np.int32).reshape(-1))
+    if off.size != tof.size + 1:
+        raise ValueError("offsets needs one more entry than tree_of")
+    handles = (C.c_void_p * max(len(trees), 1))(*[t._h for t in trees])
+    return trees, handles, off, tof
+
+
+class Batch:
+    """Many receiver subsets over several trees walked in one persistent launch.
+
+    Subset s owns rows offsets[s]..offsets[s+1]-1 of the concatenated receiver
+    list and is walked in trees[tree_of[s]] (individual timesteps, Sec. 1.2;
+    independent snapshots, Sec. 3.1).  `run` is one memset and one kernel
+    launch with no allocation or synchronisation, so it can be recorded into
+    a CUDA graph and replayed.
+    """
+
+    def __init__(self, trees, offsets, tree_of, nside: int = 2, theta: float = 0.75,
+                 flags: int = 0, stream=None):
+        self.trees, handles, self.offsets, self.tree_of = _subset_layout(trees, offsets, tree_of)
+        if not self.trees:
+            raise ValueError("a batch needs at least one tree")
+        self.device = self.trees[0].device
+        self.nb = self.trees[0].nb
+        self.total = int(self.offsets[-1]) if self.offsets.size else 0
+        self._h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(load_library().trevr2_batch_create(
+                handles, len(self.trees), self.offsets.ctypes.data_as(C.c_void_p),
+                self.tree_of.ctypes.data_as(C.c_void_p), int(self.tree_of.size), int(nside),
+                float(theta), int(flags), _stream_ptr(stream), C.byref(self._h)))
+
+    def _io(self, active, out):
+        act = _dev(active, torch.int64, self.device).reshape(-1)
+        if act.numel() != self.total:
+            raise ValueError(f"active has {act.numel()} entries, the batch has {self.total} rows")
+        if out is None:
+            out = torch.empty((self.total, self.nb), dtype=torch.float32, device=self.device)
+        elif out.shape != (self.total, self.nb) or out.dtype != torch.float32 or not (
+                out.is_cuda and out.is_contiguous()):
+            raise ValueError("out must be a contiguous CUDA float32 tensor [total, nb]")
+        return act, out
+
+    def run(self, active, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Enqueues the walk of all rows; returns J [total, nb] (not synchronised)."""
+        self._alive()
+        act, out = self._io(active, out)
+        _check(load_library().trevr2_batch_run(self._h, _ptr(act), _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def autotune(self, active, out: torch.Tensor | None = None, stream=None) -> tuple[int, int]:
+        """Times the launch shapes on a prefix and keeps the fastest: (warps, staged sources)."""
+        self._alive()
+        act, out = self._io(active, out)
+        w, m = C.c_int(0), C.c_int(0)
+        _check(load_library().trevr2_batch_autotune(self._h, _ptr(act), _ptr(out),
+                                                    _stream_ptr(stream), C.byref(w), C.byref(m)))
+        return int(w.value), int(m.value)
+
+    def status(self, stream=None):
+        self._alive()
+        _check(load_library().trevr2_batch_status(self._h, _stream_ptr(stream)))
+
+    def _alive(self):
+        if not self._h:
+            raise ValueError("batch already freed")
+
+    def free(self):
+        if getattr(self, "_h", None):
+            load_library().trevr2_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def J_batched(trees, active, offsets, tree_of, nside: int = 2, theta: float = 0.75,
+              flags: int = 0, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """One-shot batch: J [offsets[-1], nb] for every subset (synchronises unless ASYNC)."""
+    trees, handles, off, tof = _subset_layout(trees, offsets, tree_of)
+    if not trees:
+        raise ValueError("J_batched needs at least one tree")
+    dev = trees[0].device
+    act = _dev(active, torch.int64, dev).reshape(-1)
+    total = int(off[-1]) if off.size else 0
+    if act.numel() != total:
+        raise ValueError(f"active has {act.numel()} entries, offsets say {total}")
+    if out is None:
+        out = torch.empty((total, trees[0].nb), dtype=torch.float32, device=dev)
+    with torch.cuda.device(dev):
+        _check(load_library().trevr2_J_batched(
+            handles, len(trees), _ptr(act), off.ctypes.data_as(C.c_void_p),
+            tof.ctypes.data_as(C.c_void_p), int(tof.size), int(nside), float(theta), int(flags),
+            _ptr(out), _stream_ptr(stream)))
+    return out
+
+
 def build(pos, mass, kappa, lum, h=None, box_lo=None, box_size: float = 0.0, bucket: int = 12,
           device=None, stream=None) -> Tree:
     """Builds the radiation tree (Sec. 2.3) from element positions [N,3] (float64),
@@ -262,6 +394,42 @@ def build(pos, mass, kappa, lum, h=None, box_lo=None, box_size: float = 0.0, buc
 def J(tree: Tree, active, nside: int = 2, theta: float = 0.75, bands=None, flags: int = 0,
       out=None, stream=None) -> torch.Tensor:
     return tree.J(active, nside, theta, bands, flags, out, stream)
+
+
+class _JFunction(torch.autograd.Function):
+    """J as a differentiable function of the opacities and luminosities.
+
+    Forward builds the tree and walks it; backward walks it again through the
+    adjoint (no traversal is stored) and returns dLoss/dkappa and dLoss/dlum.
+    Positions, masses and sizes get no gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, kappa, lum, pos, mass, h, active, opts):
+        tree = build(pos, mass, kappa.detach(), lum.detach(), h, opts["box_lo"],
+                     opts["box_size"], opts["bucket"])
+        act = _dev(active, torch.int64, tree.device).reshape(-1)
+        out = tree.J(act, opts["nside"], opts["theta"], opts["bands"], opts["flags"])
+        ctx.tree, ctx.act, ctx.opts = tree, act, opts
+        ctx.shapes = (kappa.shape, kappa.dtype, lum.shape, lum.dtype)
+        return out
+
+    @staticmethod
+    def backward(ctx, gJ):
+        o = ctx.opts
+        gk, gl = ctx.tree.J_backward(ctx.act, gJ.contiguous(), o["nside"], o["theta"], o["bands"],
+                                     o["flags"])
+        ctx.tree.free()
+        ks, kd, ls, ld = ctx.shapes
+        return gk.reshape(ks).to(kd), gl.reshape(ls).to(ld), None, None, None, None, None
+
+
+def J_fn(pos, mass, kappa, lum, active, nside: int = 2, theta: float = 0.75, h=None, bands=None,
+         flags: int = 0, box_lo=None, box_size: float = 0.0, bucket: int = 12) -> torch.Tensor:
+    """Differentiable J [A, nbsel] (autograd gives dLoss/dkappa and dLoss/dlum)."""
+    opts = {"nside": int(nside), "theta": float(theta), "bands": bands, "flags": int(flags),
+            "box_lo": box_lo, "box_size": float(box_size), "bucket": int(bucket)}
+    return _JFunction.apply(kappa, lum, pos, mass, h, active, opts)
 
 
 def healpix_pix2vec(nside: int, device=None) -> torch.Tensor:

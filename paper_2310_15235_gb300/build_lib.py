@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libtrevr2.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["build.cu", "tables.cu", "walk.cu"]
+SOURCES = ["build.cu", "tables.cu", "walk.cu", "adjoint.cu"]
 
 
 def _nvcc() -> str:

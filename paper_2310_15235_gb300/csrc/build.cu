@@ -296,7 +296,7 @@ __global__ void k_gather_elements(const double* __restrict__ pos, const float* _
                                   double size, float h_default, int* __restrict__ inv,
                                   double* __restrict__ pos64, float4* __restrict__ pos32,
                                   float* __restrict__ Lelem, float* __restrict__ km,
-                                  float* __restrict__ hn) {
+                                  float* __restrict__ hn, float* __restrict__ ms) {
   int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (s >= N) return;
   int i = perm[s];
@@ -318,6 +318,7 @@ __global__ void k_gather_elements(const double* __restrict__ pos, const float* _
   pos32[s] = make_float4(float(u[0]), float(u[1]), float(u[2]), float(lt));
   float hh = h ? h[i] : h_default;
   hn[s] = float(double(hh) / size);
+  ms[s] = mass[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -520,6 +521,7 @@ static void free_tree(Tree* t, cudaStream_t st) {
   dfree(t->pos32, st);
   dfree(t->Lelem, st);
   dfree(t->km, st);
+  dfree(t->mass, st);
   dfree(t->hn, st);
   dfree(t->prefix, st);
   dfree(t->depth, st);
@@ -636,10 +638,11 @@ static int build_impl(Tree* t, const double* pos, const float* mass, const float
   T2_CHECK(dalloc(&t->Lelem, N * nbp, st));
   T2_CHECK(dalloc(&t->km, N * nbp, st));
   T2_CHECK(dalloc(&t->hn, N, st));
+  T2_CHECK(dalloc(&t->mass, N, st));
   if (N > 0)
     k_gather_elements<<<blocks_for(N, 256), 256, 0, st>>>(
         pos, mass, kappa, lum, h, t->perm, N, nb, nbp, t->lo[0], t->lo[1], t->lo[2], t->size,
-        h_default, t->inv, t->pos64, t->pos32, t->Lelem, t->km, t->hn); note_launch();
+        h_default, t->inv, t->pos64, t->pos32, t->Lelem, t->km, t->hn, t->mass); note_launch();
 
   // 4. bisection, one depth at a time
   int64_t cap = 0;

@@ -92,6 +92,7 @@ struct Tree {
   float* Lelem = nullptr;     // [N][nbp]
   float* km = nullptr;        // [N][nbp] kappa * m (caller units)
   float* hn = nullptr;        // [N] element size / size
+  float* mass = nullptr;      // [N] element mass (caller units)
 
   // nodes (breadth first)
   uint64_t* prefix = nullptr; // [n]

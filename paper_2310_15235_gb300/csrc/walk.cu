@@ -27,315 +27,14 @@
 // capacity of one warp's buffers are handled in further passes.
 #include <cfloat>
 #include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
 
-#include "healpix.cuh"
-#include "internal.cuh"
+#include "walk.cuh"
 
 namespace trevr2 {
-
-constexpr int kWalkWarps = 8;                 // warps per block
-constexpr int kSrcCapacity = 1024;            // sources held per warp and pass
-constexpr float kFourPi = 12.566370614359172f;
-
-struct WalkArgs {
-  const NodeW* nodes;
-  const float4* csrc;
-  const double* c64;
-  const double* B64;
-  const float* Lnode;
-  const float* alpha_leaf;
-  const float* alpha_tab;
-  const float4* pos32;
-  const double* pos64;
-  const float* Lelem;
-  const int* inv;
-  const float* hn;
-  const float* km;
-  const float4* dirs;
-  const int64_t* active;
-  int64_t A;
-  int64_t N;
-  int nside, npix, P;
-  float theta, theta2;
-  double theta64;
-  float guard_abs, guard_rel;
-  uint32_t flags;
-  int nb, nbsel;
-  int bsel[TREVR2_MAX_BANDS];
-  double inv_size2;
-  double size;
-  float* J;
-  SrcEntry* srcU;
-  int* pixU;
-  SrcEntry* srcV;
-  int M;
-  int stack_ints;   // per warp
-  int max_depth;
-  uint32_t* status;
-  unsigned long long* counter;
-};
-
-__device__ __forceinline__ float3 node_ext(uint32_t meta) {
-  const int d = int(meta & kMetaDepthMask);
-  return make_float3(__int_as_float((127 - splits_on_axis(d, 0)) << 23),
-                     __int_as_float((127 - splits_on_axis(d, 1)) << 23),
-                     __int_as_float((127 - splits_on_axis(d, 2)) << 23));
-}
-
-// FP64 opening decision, the definition evaluated without contraction.
-__device__ __noinline__ bool opens64(const WalkArgs& a, int q, const NodeW& nd, int si) {
-  const float3 e = node_ext(nd.meta);
-  const double ext[3] = {double(e.x), double(e.y), double(e.z)};
-  double s = 0.0;
-  for (int k = 0; k < 3; ++k) {
-    const double lo = double(nd.lo[k]), hi = __dadd_rn(lo, ext[k]);
-    const double x = a.pos64[3 * int64_t(si) + k];
-    double dd = 0.0;
-    if (x < lo) dd = __dsub_rn(lo, x);
-    else if (x > hi) dd = __dsub_rn(x, hi);
-    s = __dadd_rn(s, __dmul_rn(dd, dd));
-  }
-  const double d = sqrt(s);
-  return (d == 0.0) || (a.B64[q] > __dmul_rn(a.theta64, d));
-}
-
-// Coordinates for decisions on beams that lie in a plane of constant x[c]
-// (a zero beam component): half-open boxes [lo, hi) hold the beam iff
-// lo <= x[c] < hi, decided as on the FP64 position.  Box faces are
-// multiples of 2^-21, exact in FP32, and rounding to nearest never carries a
-// coordinate across one; the FP32 value only disagrees when it lands on a
-// face that the FP64 value lies just below, and then the next float below
-// restores the FP64 answer.
-__device__ __forceinline__ float3 grazing_coords(const WalkArgs& a, int si, float3 x) {
-  const double* p = a.pos64 + 3 * int64_t(si);
-  float g[3] = {x.x, x.y, x.z};
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const double f = double(g[c]) * 2097152.0;
-    if (f == floor(f) && p[c] < double(g[c])) g[c] = nextafterf(g[c], -INFINITY);
-  }
-  return make_float3(g[0], g[1], g[2]);
-}
-
-// Sec. 2.5.2: open iff d == 0 or B > theta d.
-__device__ __forceinline__ bool cell_opens(const WalkArgs& a, int q, const NodeW& nd, float3 x,
-                                           int si) {
-  const float3 e = node_ext(nd.meta);
-  const float dx = fmaxf(0.0f, fmaxf(nd.lo[0] - x.x, x.x - (nd.lo[0] + e.x)));
-  const float dy = fmaxf(0.0f, fmaxf(nd.lo[1] - x.y, x.y - (nd.lo[1] + e.y)));
-  const float dz = fmaxf(0.0f, fmaxf(nd.lo[2] - x.z, x.z - (nd.lo[2] + e.z)));
-  const float d2 = dx * dx + dy * dy + dz * dz;
-  if (d2 == 0.0f) return true;
-  const float B = nd.B;
-  const float margin = B * B - a.theta2 * d2;
-  const float g = 2.2f * B * (a.guard_abs + a.guard_rel * B);
-  if (fabsf(margin) > g) return margin > 0.0f;
-  return opens64(a, q, nd, si);
-}
-
-// Eq. intint as a kernel of r for an element of size h (normalised units).
-__device__ float soft_kernel(float r, float h) {
-  const float x = r / (0.48860251190292f * h);
-  float g;
-  if (x == 1.0f) {
-    g = 0.5f;
-  } else if (x <= 2.0f) {
-    const float xm = x - 1.0f, xp = x + 1.0f;
-    g = 0.5f * (1.0f + (x * x - 1.0f) / (4.0f * x) * logf((xm * xm) / (xp * xp)));
-  } else {
-    // sum_{m>=1} x^{-2m}/(4m^2-1): the same function without the cancellation
-    const float ix2 = 1.0f / (x * x);
-    float xm = 1.0f, s = 0.0f;
-    for (int m = 1; m < 64; ++m) {
-      xm *= ix2;
-      const float term = xm / float(4 * m * m - 1);
-      s += term;
-      if (term < 1e-9f * s) break;
-    }
-    g = s;
-  }
-  return g / (h * h);
-}
-
-// Bin one source: beam, projected distance, r/s, kernel.  Returns false for
-// a source on top of the receiver (r == 0) or with s <= 0.
-__device__ __forceinline__ bool make_source(const WalkArgs& a, float3 p, const double* p64,
-                                            float3 x, int si, int ref, SrcEntry& out, int& pix) {
-  const float vx = p.x - x.x, vy = p.y - x.y, vz = p.z - x.z;
-  const float r2 = vx * vx + vy * vy + vz * vz;
-  if (!(r2 > 0.0f)) return false;
-  const float r = sqrtf(r2);
-  int k = hp_vec2pix_f32(a.nside, vx, vy, vz, hp_guard(a.nside, r));
-  if (k < 0) {
-    const double* x64 = a.pos64 + 3 * int64_t(si);
-    k = hp_vec2pix_f64(a.nside, __dsub_rn(p64[0], x64[0]), __dsub_rn(p64[1], x64[1]),
-                       __dsub_rn(p64[2], x64[2]));
-  }
-  const float4 n = a.dirs[k];
-  const float s = vx * n.x + vy * n.y + vz * n.z;
-  if (!(s > 0.0f)) return false;
-  out.s = s;
-  out.rs = r / s;
-  out.w = (a.flags & TREVR2_SOFT) ? soft_kernel(r, a.hn[si]) : 1.0f / (kFourPi * r2);
-  out.ref = ref;
-  pix = k;
-  return true;
-}
-
-__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int u = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += u;
-  }
-  return v;
-}
-
-// Phase S for the sources whose running index is in [lo, lo + M).  Returns
-// the total number of sources of this receiver (warp-uniform).
-__device__ int phase_sources(const WalkArgs& a, float3 x, int si, int lane, int* stk, int cap,
-                             SrcEntry* U, int* Up, int lo) {
-  int sp = 1;
-  if (lane == 0) stk[0] = 0;
-  __syncwarp();
-  int emitted = 0;
-  const unsigned lt = (1u << lane) - 1u;
-  while (sp > 0) {
-    const int k = min(32, sp);
-    const int q = lane < k ? stk[sp - 1 - lane] : -1;
-    sp -= k;
-    __syncwarp();
-    int npush = 0, child = -1, leaf_first = 0, leaf_count = 0;
-    bool emit_node = false;
-    SrcEntry ent;
-    int pix = 0;
-    if (q >= 0) {
-      const NodeW nd = a.nodes[q];
-      if (nd.meta & kMetaHasL) {
-        if (!cell_opens(a, q, nd, x, si)) {
-          const float4 c = a.csrc[q];
-          emit_node = make_source(a, make_float3(c.x, c.y, c.z), a.c64 + 3 * int64_t(q), x, si, q,
-                                  ent, pix);
-        } else if (nd.meta & kMetaLeaf) {
-          leaf_first = nd.aux;
-          leaf_count = nd.count;
-        } else {
-          npush = 2;
-          child = nd.child;
-        }
-      }
-    }
-    // push opened halves
-    const int incl = warp_incl_scan(npush, lane);
-    const int tot = __shfl_sync(0xffffffffu, incl, 31);
-    if (npush) {
-      const int pos = sp + incl - npush;
-      if (pos + 2 <= cap) {
-        stk[pos] = child + 1;
-        stk[pos + 1] = child;
-      } else {
-        atomicOr(a.status, kStatusStackOverflow);
-      }
-    }
-    sp = min(sp + tot, cap);
-    // accepted luminous cells
-    {
-      const unsigned m = __ballot_sync(0xffffffffu, emit_node);
-      const int idx = emitted + __popc(m & lt) - lo;
-      if (emit_node && idx >= 0 && idx < a.M) {
-        U[idx] = ent;
-        Up[idx] = pix;
-      }
-      emitted += __popc(m);
-    }
-    // luminous elements of opened leaves
-    int maxc = leaf_count;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) maxc = max(maxc, __shfl_xor_sync(0xffffffffu, maxc, o));
-    for (int e = 0; e < maxc; ++e) {
-      bool em = false;
-      if (e < leaf_count) {
-        const int sj = leaf_first + e;
-        const float4 pj = a.pos32[sj];
-        if (pj.w > 0.0f && sj != si)
-          em = make_source(a, make_float3(pj.x, pj.y, pj.z), a.pos64 + 3 * int64_t(sj), x, si,
-                           sj | kRefElement, ent, pix);
-      }
-      const unsigned m = __ballot_sync(0xffffffffu, em);
-      const int idx = emitted + __popc(m & lt) - lo;
-      if (em && idx >= 0 && idx < a.M) {
-        U[idx] = ent;
-        Up[idx] = pix;
-      }
-      emitted += __popc(m);
-    }
-    __syncwarp();
-  }
-  return emitted;
-}
-
-// Bucket the n sources of U by beam into V; off[k] ends as the end of
-// bucket k (its start is off[k-1], or 0).  Each bucket is sorted by s.
-__device__ void bin_sources(const WalkArgs& a, int lane, const SrcEntry* U, const int* Up, int n,
-                            SrcEntry* V, int* off) {
-  const int npix = a.npix;
-  for (int k = lane; k < npix; k += 32) off[k] = 0;
-  __syncwarp();
-  for (int e = lane; e < n; e += 32) atomicAdd(&off[Up[e]], 1);
-  __syncwarp();
-  // exclusive scan of the bucket sizes
-  const int per = (npix + 31) / 32;
-  const int b0 = min(lane * per, npix), b1 = min(b0 + per, npix);
-  int sum = 0;
-  for (int k = b0; k < b1; ++k) sum += off[k];
-  const int incl = warp_incl_scan(sum, lane);
-  int run = incl - sum;
-  for (int k = b0; k < b1; ++k) {
-    const int c = off[k];
-    off[k] = run;
-    run += c;
-  }
-  __syncwarp();
-  for (int e = lane; e < n; e += 32) {
-    const int slot = atomicAdd(&off[Up[e]], 1);
-    V[slot] = U[e];
-  }
-  __syncwarp();
-  // insertion sort of each bucket by projected distance
-  for (int k = lane; k < npix; k += 32) {
-    const int s0 = k ? off[k - 1] : 0, s1 = off[k];
-    for (int i = s0 + 1; i < s1; ++i) {
-      const SrcEntry v = V[i];
-      int j = i - 1;
-      while (j >= s0 && V[j].s > v.s) {
-        V[j + 1] = V[j];
-        --j;
-      }
-      V[j + 1] = v;
-    }
-  }
-  __syncwarp();
-}
-
-template <int NBP>
-struct BandVec {
-  float v[NBP];
-};
-
-template <int NBP>
-__device__ __forceinline__ BandVec<NBP> load_bands(const float* p) {
-  BandVec<NBP> r;
-  if constexpr (NBP == 4) {
-    const float4 t = *reinterpret_cast<const float4*>(p);
-    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
-  } else if constexpr (NBP == 2) {
-    const float2 t = *reinterpret_cast<const float2*>(p);
-    r.v[0] = t.x; r.v[1] = t.y;
-  } else {
-    r.v[0] = *p;
-  }
-  return r;
-}
 
 // Phase A: lanes take beams (those with sources) from a per-warp counter.
 template <int NBP>
@@ -434,11 +133,68 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
   }
 }
 
+// J of one receiver (caller index io of the tree described by a) into
+// Jrow[0, nbsel); the warp's shared stacks and buffers are passed in.
 template <int NBP>
-__global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkArgs a) {
+__device__ __forceinline__ void walk_receiver(const WalkArgs& a, int64_t io, float* Jrow, int lane,
+                                              int* stk, int* off, int* next_beam, int* lstk,
+                                              SrcEntry* U, int* Up, SrcEntry* V) {
+  if (io < 0 || io >= a.N) {
+    if (lane == 0) atomicOr(a.status, kStatusBadActive);
+    if (lane < a.nbsel) Jrow[lane] = __int_as_float(0x7fc00000);
+    return;
+  }
+  const int si = a.inv[io];
+  const float4 xr = a.pos32[si];
+  // the receiver in FP32, on the FP64 side of every box face
+  const float3 x = grazing_coords(a, si, make_float3(xr.x, xr.y, xr.z));
+  float Js[NBP], Jc[NBP];
+#pragma unroll
+  for (int b = 0; b < NBP; ++b) Js[b] = Jc[b] = 0.0f;
+  for (int lo = 0;; lo += a.M) {
+    const int total = phase_sources(a, x, si, lane, stk, a.stack_ints, U, Up, lo);
+    const int n = min(total - lo, a.M);
+    if (n > 0) {
+      bin_sources(a, lane, U, Up, n, V, off);
+      if (lane == 0) *next_beam = 32;
+      __syncwarp();
+      phase_absorb<NBP>(a, x, si, lane, lstk, V, off, next_beam, Js, Jc);
+      __syncwarp();
+    }
+    if (lo + a.M >= total) break;
+  }
+  // FP64 reduction of the lane partial sums
+  double Jd[NBP];
+#pragma unroll
+  for (int b = 0; b < NBP; ++b) {
+    double v = double(Js[b]) - double(Jc[b]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    Jd[b] = v;
+  }
+  if (lane < a.nbsel) {
+    const int b = a.bsel[lane];
+    double v = 0.0;
+#pragma unroll
+    for (int c = 0; c < NBP; ++c)
+      if (c == b) v = Jd[c];
+    v *= a.inv_size2;
+    if (a.flags & TREVR2_THICK) {
+      // Eq. taucorr: <I> = I(0) (1 - e^{-tau})/tau, tau = kappa m / h^2
+      const double h = double(a.hn[si]) * a.size;
+      const double tau = double(a.km[int64_t(si) * NBP + b]) / (h * h);
+      if (tau > 0.0) v *= -expm1(-tau) / tau;
+    }
+    Jrow[lane] = float(v);
+  }
+}
+
+// One warp per receiver, receivers from a global counter.
+template <int NBP, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_walk(WalkArgs a) {
   extern __shared__ int smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t gw = int64_t(blockIdx.x) * kWalkWarps + wib;
+  const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;
   int* wsm = smem + wib * (a.stack_ints + a.npix + 1);
   int* stk = wsm;
   int* off = wsm + a.stack_ints;
@@ -452,126 +208,179 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk(WalkArgs a) {
     if (lane == 0) slot = atomicAdd(a.counter, 1ull);
     slot = __shfl_sync(0xffffffffu, slot, 0);
     if (slot >= (unsigned long long)a.A) break;
-    const int64_t io = a.active[slot];
-    if (io < 0 || io >= a.N) {
-      if (lane == 0) atomicOr(a.status, kStatusBadActive);
-      if (lane < a.nbsel) a.J[int64_t(slot) * a.nbsel + lane] = __int_as_float(0x7fc00000);
-      continue;
-    }
-    const int si = a.inv[io];
-    const float4 xr = a.pos32[si];
-    // the receiver in FP32, on the FP64 side of every box face
-    const float3 x = grazing_coords(a, si, make_float3(xr.x, xr.y, xr.z));
-    float Js[NBP], Jc[NBP];
-#pragma unroll
-    for (int b = 0; b < NBP; ++b) Js[b] = Jc[b] = 0.0f;
-    for (int lo = 0;; lo += a.M) {
-      const int total = phase_sources(a, x, si, lane, stk, a.stack_ints, U, Up, lo);
-      const int n = min(total - lo, a.M);
-      if (n > 0) {
-        bin_sources(a, lane, U, Up, n, V, off);
-        if (lane == 0) *next_beam = 32;
-        __syncwarp();
-        phase_absorb<NBP>(a, x, si, lane, lstk, V, off, next_beam, Js, Jc);
-        __syncwarp();
-      }
-      if (lo + a.M >= total) break;
-    }
-    // FP64 reduction of the lane partial sums
-    double Jd[NBP];
-#pragma unroll
-    for (int b = 0; b < NBP; ++b) {
-      double v = double(Js[b]) - double(Jc[b]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      Jd[b] = v;
-    }
-    if (lane < a.nbsel) {
-      const int b = a.bsel[lane];
-      double v = 0.0;
-#pragma unroll
-      for (int c = 0; c < NBP; ++c)
-        if (c == b) v = Jd[c];
-      v *= a.inv_size2;
-      if (a.flags & TREVR2_THICK) {
-        // Eq. taucorr: <I> = I(0) (1 - e^{-tau})/tau, tau = kappa m / h^2
-        const double h = double(a.hn[si]) * a.size;
-        const double tau = double(a.km[int64_t(si) * NBP + b]) / (h * h);
-        if (tau > 0.0) v *= -expm1(-tau) / tau;
-      }
-      a.J[int64_t(slot) * a.nbsel + lane] = float(v);
-    }
+    walk_receiver<NBP>(a, a.active[slot], a.J + int64_t(slot) * a.nbsel, lane, stk, off, next_beam,
+                       lstk, U, Up, V);
   }
 }
 
-static bool valid_nside(int nside) {
+// Many receiver subsets over several trees in one launch (individual
+// timesteps over independent snapshots, Sec. 1.2 and Sec. 3.1): receiver r
+// of the concatenated list belongs to the subset s with
+// offsets[s] <= r < offsets[s + 1] and is walked in tree tree_of[s].
+constexpr int kMaxBatchTrees = TREVR2_MAX_BATCH_TREES;
+
+struct BatchArgs {
+  WalkArgs tree[kMaxBatchTrees];  // per-tree arguments (their active/J fields unused)
+  const int64_t* active;          // [total] concatenated receiver indices
+  const int64_t* offsets;         // [nsub + 1]
+  const int* tree_of;             // [nsub]
+  int nsub;
+  int64_t total;
+  float* J;                       // [total][nbsel]
+  int nbsel;
+  SrcEntry* srcU;
+  int* pixU;
+  SrcEntry* srcV;
+  int M;
+  int stack_ints;
+  int npix;
+  int max_depth;
+  unsigned long long* counter;
+};
+
+template <int NBP, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_walk_batched(const __grid_constant__ BatchArgs B) {
+  extern __shared__ int smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;
+  int* wsm = smem + wib * (B.stack_ints + B.npix + 1);
+  int* stk = wsm;
+  int* off = wsm + B.stack_ints;
+  int* next_beam = off + B.npix;
+  int* lstk = stk + lane * (B.max_depth + 2);
+  SrcEntry* U = B.srcU + gw * B.M;
+  int* Up = B.pixU + gw * B.M;
+  SrcEntry* V = B.srcV + gw * B.M;
+  for (;;) {
+    unsigned long long r = 0;
+    int t = 0;
+    if (lane == 0) {
+      r = atomicAdd(B.counter, 1ull);
+      if (r < (unsigned long long)B.total) {
+        int lo = 0, hi = B.nsub;  // offsets[lo] <= r < offsets[hi]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (B.offsets[mid] <= int64_t(r)) lo = mid; else hi = mid;
+        }
+        t = B.tree_of[lo];
+      }
+    }
+    r = __shfl_sync(0xffffffffu, r, 0);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (r >= (unsigned long long)B.total) break;
+    walk_receiver<NBP>(B.tree[t], B.active[r], B.J + int64_t(r) * B.nbsel, lane, stk, off,
+                       next_beam, lstk, U, Up, V);
+  }
+}
+
+bool valid_nside(int nside) {
   return nside >= 1 && nside <= TREVR2_MAX_NSIDE && (nside & (nside - 1)) == 0;
+}
+
+// Per-tree walk arguments for one nside (everything but the receivers, the
+// output and the buffers).
+void fill_walk_args(const Tree* t, const Table* tb, int nside, float theta, const int* bsel,
+                    int nbsel, uint32_t flags, int M, WalkArgs* a) {
+  std::memset(a, 0, sizeof(WalkArgs));
+  a->nodes = t->nodes;
+  a->csrc = t->csrc;
+  a->c64 = t->c64;
+  a->B64 = t->B64;
+  a->Lnode = t->Lnode;
+  a->alpha_leaf = t->alpha_leaf;
+  a->alpha_tab = tb->alpha;
+  a->pos32 = t->pos32;
+  a->pos64 = t->pos64;
+  a->Lelem = t->Lelem;
+  a->inv = t->inv;
+  a->hn = t->hn;
+  a->km = t->km;
+  a->dirs = tb->dirs;
+  a->N = t->N;
+  a->nside = nside;
+  a->npix = 12 * nside * nside;
+  a->P = a->npix / 2;
+  a->theta = theta;
+  a->theta2 = theta * theta;
+  a->theta64 = double(theta);
+  a->guard_abs = 2e-7f * theta + 2e-7f;
+  a->guard_rel = 2e-6f;
+  a->flags = flags;
+  a->nb = t->nb;
+  a->nbsel = nbsel;
+  for (int b = 0; b < TREVR2_MAX_BANDS; ++b) a->bsel[b] = b < nbsel ? bsel[b] : 0;
+  a->inv_size2 = 1.0 / (t->size * t->size);
+  a->size = t->size;
+  a->M = M;
+  a->max_depth = t->max_depth;
+  a->stack_ints = 64 * (t->max_depth + 2);
+  a->status = t->status;
+  a->counter = t->counter;
+}
+
+template <int NBP>
+static const void* walk_kernel_nbp(int warps, bool batched) {
+  if (batched)
+    return warps == 4 ? reinterpret_cast<const void*>(&k_walk_batched<NBP, 4>)
+                      : reinterpret_cast<const void*>(&k_walk_batched<NBP, 8>);
+  return warps == 4 ? reinterpret_cast<const void*>(&k_walk<NBP, 4>)
+                    : reinterpret_cast<const void*>(&k_walk<NBP, 8>);
+}
+
+static const void* walk_kernel(int nbp, int warps, bool batched) {
+  return nbp == 1 ? walk_kernel_nbp<1>(warps, batched)
+       : nbp == 2 ? walk_kernel_nbp<2>(warps, batched)
+                  : walk_kernel_nbp<4>(warps, batched);
+}
+
+
+// Shared memory attribute and resident blocks per SM of a walk kernel.
+int config_walk_kernel(const void* fn, int warps, size_t smem, int* per_sm, int* sms) {
+  int dev = 0, max_smem = 0;
+  T2_CUDA(cudaGetDevice(&dev));
+  T2_CUDA(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev));
+  T2_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (smem > size_t(max_smem)) {
+    set_error("trevr2: the walk needs %zu bytes of shared memory per block (tree too deep for "
+              "this nside)", smem);
+    return TREVR2_EUNSUPPORTED;
+  }
+  T2_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  *per_sm = 0;
+  T2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, warps * 32, smem));
+  if (*per_sm < 1) *per_sm = 1;
+  return TREVR2_OK;
+}
+
+// Walk buffers: per warp, M source records in and out and their beams.
+static size_t walk_buffer_bytes(size_t warps, int M) {
+  return warps * size_t(M) * (2 * sizeof(SrcEntry) + sizeof(int));
+}
+
+static void place_walk_buffers(char* base, size_t warps, int M, SrcEntry** U, SrcEntry** V,
+                               int** Up) {
+  *U = reinterpret_cast<SrcEntry*>(base);
+  *V = reinterpret_cast<SrcEntry*>(base + warps * M * sizeof(SrcEntry));
+  *Up = reinterpret_cast<int*>(base + 2 * warps * M * sizeof(SrcEntry));
 }
 
 static int launch_walk(Tree* t, Table* tb, const int64_t* active, int64_t A, int nside,
                        float theta, const int* bsel, int nbsel, uint32_t flags, float* J,
                        cudaStream_t st) {
-  int dev = 0, sms = 0;
-  T2_CUDA(cudaGetDevice(&dev));
-  T2_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   WalkArgs a;
-  a.nodes = t->nodes;
-  a.csrc = t->csrc;
-  a.c64 = t->c64;
-  a.B64 = t->B64;
-  a.Lnode = t->Lnode;
-  a.alpha_leaf = t->alpha_leaf;
-  a.alpha_tab = tb->alpha;
-  a.pos32 = t->pos32;
-  a.pos64 = t->pos64;
-  a.Lelem = t->Lelem;
-  a.inv = t->inv;
-  a.hn = t->hn;
-  a.km = t->km;
-  a.dirs = tb->dirs;
+  fill_walk_args(t, tb, nside, theta, bsel, nbsel, flags, kSrcCapacity, &a);
   a.active = active;
   a.A = A;
-  a.N = t->N;
-  a.nside = nside;
-  a.npix = 12 * nside * nside;
-  a.P = a.npix / 2;
-  a.theta = theta;
-  a.theta2 = theta * theta;
-  a.theta64 = double(theta);
-  a.guard_abs = 2e-7f * theta + 2e-7f;
-  a.guard_rel = 2e-6f;
-  a.flags = flags;
-  a.nb = t->nb;
-  a.nbsel = nbsel;
-  for (int b = 0; b < TREVR2_MAX_BANDS; ++b) a.bsel[b] = b < nbsel ? bsel[b] : 0;
-  a.inv_size2 = 1.0 / (t->size * t->size);
-  a.size = t->size;
   a.J = J;
-  a.M = kSrcCapacity;
-  a.max_depth = t->max_depth;
-  a.stack_ints = 64 * (t->max_depth + 2);
-  a.status = t->status;
-  a.counter = t->counter;
-  const size_t smem = size_t(kWalkWarps) * (a.stack_ints + a.npix + 1) * sizeof(int);
-  int max_smem = 0;
-  T2_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (smem > size_t(max_smem)) {
-    set_error("trevr2_J: tree depth %d with nside %d needs %zu bytes of shared memory per block",
-              t->max_depth, nside, smem);
-    return TREVR2_EUNSUPPORTED;
-  }
-  const void* fn = t->nbp == 1 ? reinterpret_cast<const void*>(&k_walk<1>)
-                 : t->nbp == 2 ? reinterpret_cast<const void*>(&k_walk<2>)
-                               : reinterpret_cast<const void*>(&k_walk<4>);
-  T2_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-  int per_sm = 0;
-  T2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kWalkWarps * 32, smem));
-  if (per_sm < 1) per_sm = 1;
+  const void* fn = walk_kernel(t->nbp, kWalkWarps, false);
+  const size_t smem = walk_smem(kWalkWarps, a.stack_ints, a.npix);
+  int per_sm = 0, sms = 0;
+  T2_CHECK(config_walk_kernel(fn, kWalkWarps, smem, &per_sm, &sms));
   int64_t blocks = int64_t(sms) * per_sm;
   blocks = std::min<int64_t>(blocks, (A + kWalkWarps - 1) / kWalkWarps);
   blocks = std::max<int64_t>(blocks, 1);
   const size_t warps = size_t(blocks) * kWalkWarps;
-  const size_t need = warps * a.M * (2 * sizeof(SrcEntry) + sizeof(int));
+  const size_t need = walk_buffer_bytes(warps, a.M);
   if (t->scratch_bytes < need) {
     if (t->scratch) cudaFreeAsync(t->scratch, st);
     t->scratch = nullptr;
@@ -580,10 +389,7 @@ static int launch_walk(Tree* t, Table* tb, const int64_t* active, int64_t A, int
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(walk buffers)");
     t->scratch_bytes = need;
   }
-  char* base = static_cast<char*>(t->scratch);
-  a.srcU = reinterpret_cast<SrcEntry*>(base);
-  a.srcV = reinterpret_cast<SrcEntry*>(base + warps * a.M * sizeof(SrcEntry));
-  a.pixU = reinterpret_cast<int*>(base + 2 * warps * a.M * sizeof(SrcEntry));
+  place_walk_buffers(static_cast<char*>(t->scratch), warps, a.M, &a.srcU, &a.srcV, &a.pixU);
   T2_CUDA(cudaMemsetAsync(t->counter, 0, sizeof(unsigned long long), st));
   void* args[] = {&a};
   T2_CUDA(cudaLaunchKernel(fn, dim3(unsigned(blocks)), dim3(kWalkWarps * 32), args, smem, st));
@@ -591,7 +397,7 @@ static int launch_walk(Tree* t, Table* tb, const int64_t* active, int64_t A, int
   return TREVR2_OK;
 }
 
-static int read_status(Tree* t, cudaStream_t st) {
+int read_status(Tree* t, cudaStream_t st) {
   uint32_t s = 0;
   T2_CUDA(cudaMemcpyAsync(&s, t->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   T2_CUDA(cudaStreamSynchronize(st));
@@ -662,6 +468,312 @@ extern "C" int trevr2_J(trevr2_tree* tree, const int64_t* active, int64_t A, int
   T2_CHECK(launch_walk(t, tb, active, A, nside, theta, bsel, nbsel, flags, J, st));
   if (flags & TREVR2_ASYNC) return TREVR2_OK;
   return read_status(t, st);
+}
+
+// ---------------------------------------------------------------------------
+// Batches: many active subsets over several trees in one persistent launch.
+namespace trevr2 {
+
+struct Batch {
+  std::vector<Tree*> trees;
+  int nside = 0;
+  int nsub = 0;
+  int64_t total = 0;
+  int nbp = 1;
+  int64_t* d_offsets = nullptr;
+  int* d_tree_of = nullptr;
+  unsigned long long* counter = nullptr;
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  int warps = kWalkWarps;  // chosen launch shape
+  int M = kSrcCapacity;    // chosen source staging depth
+  const void* fn = nullptr;  // kernel, shared memory and grid of that shape
+  size_t smem = 0;
+  int64_t blocks = 0;
+  cudaStream_t last_stream = nullptr;
+  BatchArgs args;
+};
+
+// Grid and buffers of a batch launch for (warps, M); grows the buffers.
+static int batch_shape(Batch* b, int warps, int M, int64_t limit, const void** fn, size_t* smem,
+                       int64_t* blocks, cudaStream_t st) {
+  *fn = walk_kernel(b->nbp, warps, true);
+  *smem = walk_smem(warps, b->args.stack_ints, b->args.npix);
+  int per_sm = 0, sms = 0;
+  T2_CHECK(config_walk_kernel(*fn, warps, *smem, &per_sm, &sms));
+  int64_t g = int64_t(sms) * per_sm;
+  g = std::min<int64_t>(g, (limit + warps - 1) / warps);
+  *blocks = std::max<int64_t>(g, 1);
+  const size_t nw = size_t(*blocks) * warps;
+  const size_t need = walk_buffer_bytes(nw, M);
+  if (b->scratch_bytes < need) {
+    if (b->scratch) cudaFreeAsync(b->scratch, st);
+    b->scratch = nullptr;
+    b->scratch_bytes = 0;
+    cudaError_t e = cudaMallocAsync(&b->scratch, need, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(batch walk buffers)");
+    b->scratch_bytes = need;
+  }
+  place_walk_buffers(static_cast<char*>(b->scratch), nw, M, &b->args.srcU, &b->args.srcV,
+                     &b->args.pixU);
+  b->args.M = M;
+  for (size_t i = 0; i < b->trees.size(); ++i) b->args.tree[i].M = M;
+  return TREVR2_OK;
+}
+
+// Fixes the launch shape (warps, M) for the first `limit` receivers.
+static int batch_select(Batch* b, int warps, int M, int64_t limit, cudaStream_t st) {
+  T2_CHECK(batch_shape(b, warps, M, limit, &b->fn, &b->smem, &b->blocks, st));
+  b->warps = warps;
+  b->M = M;
+  b->args.total = limit;
+  return TREVR2_OK;
+}
+
+// Enqueues the walk in the selected shape: one memset and one kernel, with
+// no allocation, synchronisation or attribute call, so that it can be
+// recorded into a CUDA graph.
+static int batch_enqueue(Batch* b, const int64_t* active, float* J, cudaStream_t st) {
+  b->args.active = active;
+  b->args.J = J;
+  T2_CUDA(cudaMemsetAsync(b->counter, 0, sizeof(unsigned long long), st));
+  void* argv[] = {&b->args};
+  T2_CUDA(cudaLaunchKernel(b->fn, dim3(unsigned(b->blocks)), dim3(b->warps * 32), argv, b->smem, st));
+  note_launch();
+  return TREVR2_OK;
+}
+
+static void free_batch(Batch* b, cudaStream_t st) {
+  dfree(b->d_offsets, st);
+  dfree(b->d_tree_of, st);
+  dfree(b->counter, st);
+  if (b->scratch) cudaFreeAsync(b->scratch, st);
+  b->scratch = nullptr;
+}
+
+}  // namespace trevr2
+
+extern "C" int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const int64_t* offsets,
+                                   const int* tree_of, int nsub, int nside, float theta,
+                                   uint32_t flags, void* stream, trevr2_batch** out) {
+  clear_error();
+  if (!out) {
+    set_error("trevr2_batch_create: out is NULL");
+    return TREVR2_EINVAL;
+  }
+  *out = nullptr;
+  if (!trees || ntrees < 1 || nsub < 0 || (nsub > 0 && (!offsets || !tree_of))) {
+    set_error("trevr2_batch_create: NULL arrays, ntrees < 1 or nsub < 0");
+    return TREVR2_EINVAL;
+  }
+  if (ntrees > kMaxBatchTrees) {
+    set_error("trevr2_batch_create: at most %d trees per batch", kMaxBatchTrees);
+    return TREVR2_EUNSUPPORTED;
+  }
+  if (!valid_nside(nside)) {
+    set_error("trevr2_batch_create: nside %d is not a power of two in [1, %d]", nside,
+              TREVR2_MAX_NSIDE);
+    return nside > TREVR2_MAX_NSIDE ? TREVR2_EUNSUPPORTED : TREVR2_EINVAL;
+  }
+  if (!(theta > 0.0f) || !std::isfinite(theta) || (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_ASYNC))) {
+    set_error("trevr2_batch_create: theta must be positive and finite, flags SOFT|THICK|ASYNC");
+    return TREVR2_EINVAL;
+  }
+  const int nb = reinterpret_cast<Tree*>(trees[0])->nb;
+  for (int i = 0; i < ntrees; ++i) {
+    if (!trees[i] || reinterpret_cast<Tree*>(trees[i])->nb != nb) {
+      set_error("trevr2_batch_create: tree %d is NULL or has a different band count", i);
+      return TREVR2_EINVAL;
+    }
+  }
+  if (nsub > 0 && offsets[0] != 0) {
+    set_error("trevr2_batch_create: offsets[0] must be 0");
+    return TREVR2_EINVAL;
+  }
+  for (int s = 0; s < nsub; ++s) {
+    if (offsets[s + 1] < offsets[s] || tree_of[s] < 0 || tree_of[s] >= ntrees) {
+      set_error("trevr2_batch_create: offsets must not decrease and tree_of must index the trees "
+                "(subset %d)", s);
+      return TREVR2_EINVAL;
+    }
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Batch* b = new (std::nothrow) Batch();
+  if (!b) {
+    set_error("trevr2_batch_create: host allocation failed");
+    return TREVR2_ENOMEM;
+  }
+  auto fail = [&](int rc) {
+    std::string msg = trevr2_last_error();
+    free_batch(b, st);
+    delete b;
+    set_error("%s", msg.c_str());
+    return rc;
+  };
+  b->nside = nside;
+  b->nsub = nsub;
+  b->total = nsub > 0 ? offsets[nsub] : 0;
+  b->nbp = nbp_of(nb);
+  b->last_stream = st;
+  std::memset(&b->args, 0, sizeof(BatchArgs));
+  int max_depth = 0;
+  int bsel[TREVR2_MAX_BANDS];
+  for (int k = 0; k < nb; ++k) bsel[k] = k;
+  for (int i = 0; i < ntrees; ++i) {
+    Tree* t = reinterpret_cast<Tree*>(trees[i]);
+    t->last_stream = st;
+    b->trees.push_back(t);
+    max_depth = std::max(max_depth, t->max_depth);
+    Table* tb = nullptr;
+    int rc = ensure_table(t, nside, st, &tb);
+    if (rc) return fail(rc);
+    fill_walk_args(t, tb, nside, theta, bsel, nb, flags & ~TREVR2_ASYNC, kSrcCapacity, &b->args.tree[i]);
+  }
+  // one shared-memory layout for all trees: the deepest one's
+  for (int i = 0; i < ntrees; ++i) {
+    b->args.tree[i].max_depth = max_depth;
+    b->args.tree[i].stack_ints = 64 * (max_depth + 2);
+  }
+  b->args.max_depth = max_depth;
+  b->args.stack_ints = 64 * (max_depth + 2);
+  b->args.npix = 12 * nside * nside;
+  b->args.nbsel = nb;
+  b->args.nsub = nsub;
+  int rc = dalloc(&b->d_offsets, size_t(nsub) + 1, st);
+  if (!rc) rc = dalloc(&b->d_tree_of, size_t(std::max(nsub, 1)), st);
+  if (!rc) rc = dalloc(&b->counter, 1, st);
+  if (rc) return fail(rc);
+  if (nsub > 0) {
+    cudaError_t e = cudaMemcpyAsync(b->d_offsets, offsets, (size_t(nsub) + 1) * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->d_tree_of, tree_of, size_t(nsub) * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpyAsync(batch metadata)"));
+  }
+  b->args.offsets = b->d_offsets;
+  b->args.tree_of = b->d_tree_of;
+  b->args.counter = b->counter;
+  // the default shape and its buffers, so that run() never allocates
+  rc = batch_select(b, kWalkWarps, kSrcCapacity, b->total, st);
+  if (rc) return fail(rc);
+  *out = reinterpret_cast<trevr2_batch*>(b);
+  return TREVR2_OK;
+}
+
+extern "C" int trevr2_batch_run(trevr2_batch* batch, const int64_t* active, float* J, void* stream) {
+  clear_error();
+  if (!batch) {
+    set_error("trevr2_batch_run: batch is NULL");
+    return TREVR2_EINVAL;
+  }
+  Batch* b = reinterpret_cast<Batch*>(batch);
+  if (b->total > 0 && (!active || !J)) {
+    set_error("trevr2_batch_run: NULL active or J");
+    return TREVR2_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  b->last_stream = st;
+  if (b->total == 0) return TREVR2_OK;
+  return batch_enqueue(b, active, J, st);
+}
+
+extern "C" int trevr2_batch_autotune(trevr2_batch* batch, const int64_t* active, float* J,
+                                     void* stream, int* warps_out, int* staging_out) {
+  clear_error();
+  if (!batch) {
+    set_error("trevr2_batch_autotune: batch is NULL");
+    return TREVR2_EINVAL;
+  }
+  Batch* b = reinterpret_cast<Batch*>(batch);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  b->last_stream = st;
+  if (b->total > 0 && (!active || !J)) {
+    set_error("trevr2_batch_autotune: NULL active or J");
+    return TREVR2_EINVAL;
+  }
+  if (b->total > 0) {
+    // time each (warps per block, source staging depth) on a prefix of the
+    // work and keep the fastest
+    const int64_t limit = std::min<int64_t>(b->total, 65536);
+    const int cand_w[2] = {4, 8};
+    const int cand_m[3] = {512, 1024, 2048};
+    cudaEvent_t e0, e1;
+    T2_CUDA(cudaEventCreate(&e0));
+    T2_CUDA(cudaEventCreate(&e1));
+    float best = INFINITY;
+    int bw = b->warps, bm = b->M;
+    for (int w : cand_w)
+      for (int m : cand_m) {
+        int rc = batch_select(b, w, m, limit, st);
+        if (!rc) rc = batch_enqueue(b, active, J, st);  // warm-up
+        if (!rc) {
+          cudaError_t e = cudaEventRecord(e0, st);
+          if (e == cudaSuccess) rc = batch_enqueue(b, active, J, st);
+          if (e == cudaSuccess && !rc) e = cudaEventRecord(e1, st);
+          if (e != cudaSuccess) rc = cuda_fail(e, "cudaEventRecord");
+        }
+        if (rc) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return rc;
+        }
+        T2_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        T2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          bw = w;
+          bm = m;
+        }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the chosen shape and its buffers at full size
+    T2_CHECK(batch_select(b, bw, bm, b->total, st));
+    T2_CUDA(cudaStreamSynchronize(st));
+  }
+  if (warps_out) *warps_out = b->warps;
+  if (staging_out) *staging_out = b->M;
+  return TREVR2_OK;
+}
+
+extern "C" int trevr2_batch_status(trevr2_batch* batch, void* stream) {
+  clear_error();
+  if (!batch) {
+    set_error("trevr2_batch_status: batch is NULL");
+    return TREVR2_EINVAL;
+  }
+  Batch* b = reinterpret_cast<Batch*>(batch);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = TREVR2_OK;
+  for (Tree* t : b->trees) {
+    const int r = read_status(t, st);
+    if (r != TREVR2_OK && rc == TREVR2_OK) rc = r;
+  }
+  return rc;
+}
+
+extern "C" int trevr2_batch_free(trevr2_batch* batch) {
+  clear_error();
+  if (!batch) return TREVR2_OK;
+  Batch* b = reinterpret_cast<Batch*>(batch);
+  free_batch(b, b->last_stream);
+  delete b;
+  return TREVR2_OK;
+}
+
+extern "C" int trevr2_J_batched(trevr2_tree* const* trees, int ntrees, const int64_t* active,
+                                const int64_t* offsets, const int* tree_of, int nsub, int nside,
+                                float theta, uint32_t flags, float* J, void* stream) {
+  trevr2_batch* b = nullptr;
+  T2_CHECK(trevr2_batch_create(trees, ntrees, offsets, tree_of, nsub, nside, theta, flags, stream, &b));
+  int rc = trevr2_batch_run(b, active, J, stream);
+  if (rc == TREVR2_OK && !(flags & TREVR2_ASYNC)) rc = trevr2_batch_status(b, stream);
+  std::string msg = trevr2_last_error();
+  trevr2_batch_free(b);
+  if (rc != TREVR2_OK) set_error("%s", msg.c_str());
+  return rc;
 }
 
 extern "C" int trevr2_status(trevr2_tree* tree, void* stream) {
@@ -738,65 +850,18 @@ static int launch_walk_noalloc(Tree* t, Table* tb, const int64_t* active, int64_
                                cudaStream_t st) {
   void* scratch = nullptr;
   T2_CHECK(noalloc_scratch(&scratch));
-  int dev = 0, sms = 0;
-  T2_CUDA(cudaGetDevice(&dev));
-  T2_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   WalkArgs a;
-  a.nodes = t->nodes;
-  a.csrc = t->csrc;
-  a.c64 = t->c64;
-  a.B64 = t->B64;
-  a.Lnode = t->Lnode;
-  a.alpha_leaf = t->alpha_leaf;
-  a.alpha_tab = tb->alpha;
-  a.pos32 = t->pos32;
-  a.pos64 = t->pos64;
-  a.Lelem = t->Lelem;
-  a.inv = t->inv;
-  a.hn = t->hn;
-  a.km = t->km;
-  a.dirs = tb->dirs;
+  fill_walk_args(t, tb, nside, theta, bsel, nbsel, flags, kNoAllocSources, &a);
   a.active = active;
   a.A = A;
-  a.N = t->N;
-  a.nside = nside;
-  a.npix = 12 * nside * nside;
-  a.P = a.npix / 2;
-  a.theta = theta;
-  a.theta2 = theta * theta;
-  a.theta64 = double(theta);
-  a.guard_abs = 2e-7f * theta + 2e-7f;
-  a.guard_rel = 2e-6f;
-  a.flags = flags;
-  a.nb = t->nb;
-  a.nbsel = nbsel;
-  for (int b = 0; b < TREVR2_MAX_BANDS; ++b) a.bsel[b] = b < nbsel ? bsel[b] : 0;
-  a.inv_size2 = 1.0 / (t->size * t->size);
-  a.size = t->size;
   a.J = J;
-  a.M = kNoAllocSources;
-  a.max_depth = t->max_depth;
-  a.stack_ints = 64 * (t->max_depth + 2);
-  a.status = t->status;
-  a.counter = t->counter;
-  const size_t smem = size_t(kWalkWarps) * (a.stack_ints + a.npix + 1) * sizeof(int);
-  int max_smem = 0;
-  T2_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (smem > size_t(max_smem)) {
-    set_error("trevr2_J_noalloc: tree depth %d with nside %d needs %zu bytes of shared memory",
-              t->max_depth, nside, smem);
-    return TREVR2_EUNSUPPORTED;
-  }
-  const void* fn = t->nbp == 1 ? reinterpret_cast<const void*>(&k_walk<1>)
-                 : t->nbp == 2 ? reinterpret_cast<const void*>(&k_walk<2>)
-                               : reinterpret_cast<const void*>(&k_walk<4>);
-  T2_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-  int per_sm = 0;
-  T2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kWalkWarps * 32, smem));
-  if (per_sm < 1) per_sm = 1;
+  const void* fn = walk_kernel(t->nbp, kWalkWarps, false);
+  const size_t smem = walk_smem(kWalkWarps, a.stack_ints, a.npix);
+  int per_sm = 0, sms = 0;
+  T2_CHECK(config_walk_kernel(fn, kWalkWarps, smem, &per_sm, &sms));
   // The grid is capped by what the fixed array holds; the kernel loops over
   // receivers and passes over sources, so any A and any source count fit.
-  const size_t per_block = size_t(kWalkWarps) * a.M * (2 * sizeof(SrcEntry) + sizeof(int));
+  const size_t per_block = walk_buffer_bytes(kWalkWarps, a.M);
   const int64_t max_blocks = int64_t(kNoAllocScratchBytes / per_block);
   if (max_blocks < 1) {
     set_error("trevr2_J_noalloc: one block needs %zu bytes of walk buffers, the fixed array "
@@ -808,10 +873,7 @@ static int launch_walk_noalloc(Tree* t, Table* tb, const int64_t* active, int64_
   blocks = std::min<int64_t>(blocks, max_blocks);
   blocks = std::max<int64_t>(blocks, 1);
   const size_t warps = size_t(blocks) * kWalkWarps;
-  char* base = static_cast<char*>(scratch);
-  a.srcU = reinterpret_cast<SrcEntry*>(base);
-  a.srcV = reinterpret_cast<SrcEntry*>(base + warps * a.M * sizeof(SrcEntry));
-  a.pixU = reinterpret_cast<int*>(base + 2 * warps * a.M * sizeof(SrcEntry));
+  place_walk_buffers(static_cast<char*>(scratch), warps, a.M, &a.srcU, &a.srcV, &a.pixU);
   T2_CUDA(cudaMemsetAsync(t->counter, 0, sizeof(unsigned long long), st));
   void* args[] = {&a};
   T2_CUDA(cudaLaunchKernel(fn, dim3(unsigned(blocks)), dim3(kWalkWarps * 32), args, smem, st));

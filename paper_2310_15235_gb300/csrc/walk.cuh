@@ -1,0 +1,337 @@
+// Device pieces of the TREVR2 walk shared by the forward walk (walk.cu) and
+// the adjoint walk (adjoint.cu): walk arguments, the opening criterion
+// (Sec. 2.5.2), the source kernel (Eq. intint), source binning by HEALPix
+// beam (Sec. 2.5.1) and the warp-cooperative source phase.
+#pragma once
+
+#include <cfloat>
+#include <cmath>
+
+#include "healpix.cuh"
+#include "internal.cuh"
+
+namespace trevr2 {
+
+constexpr int kWalkWarps = 8;                 // warps per block
+constexpr int kSrcCapacity = 1024;            // sources held per warp and pass
+constexpr float kFourPi = 12.566370614359172f;
+
+struct WalkArgs {
+  const NodeW* nodes;
+  const float4* csrc;
+  const double* c64;
+  const double* B64;
+  const float* Lnode;
+  const float* alpha_leaf;
+  const float* alpha_tab;
+  const float4* pos32;
+  const double* pos64;
+  const float* Lelem;
+  const int* inv;
+  const float* hn;
+  const float* km;
+  const float4* dirs;
+  const int64_t* active;
+  int64_t A;
+  int64_t N;
+  int nside, npix, P;
+  float theta, theta2;
+  double theta64;
+  float guard_abs, guard_rel;
+  uint32_t flags;
+  int nb, nbsel;
+  int bsel[TREVR2_MAX_BANDS];
+  double inv_size2;
+  double size;
+  float* J;
+  SrcEntry* srcU;
+  int* pixU;
+  SrcEntry* srcV;
+  int M;
+  int stack_ints;   // per warp
+  int max_depth;
+  uint32_t* status;
+  unsigned long long* counter;
+};
+
+__device__ __forceinline__ float3 node_ext(uint32_t meta) {
+  const int d = int(meta & kMetaDepthMask);
+  return make_float3(__int_as_float((127 - splits_on_axis(d, 0)) << 23),
+                     __int_as_float((127 - splits_on_axis(d, 1)) << 23),
+                     __int_as_float((127 - splits_on_axis(d, 2)) << 23));
+}
+
+// FP64 opening decision, the definition evaluated without contraction.
+static __device__ __noinline__ bool opens64(const WalkArgs& a, int q, const NodeW& nd, int si) {
+  const float3 e = node_ext(nd.meta);
+  const double ext[3] = {double(e.x), double(e.y), double(e.z)};
+  double s = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const double lo = double(nd.lo[k]), hi = __dadd_rn(lo, ext[k]);
+    const double x = a.pos64[3 * int64_t(si) + k];
+    double dd = 0.0;
+    if (x < lo) dd = __dsub_rn(lo, x);
+    else if (x > hi) dd = __dsub_rn(x, hi);
+    s = __dadd_rn(s, __dmul_rn(dd, dd));
+  }
+  const double d = sqrt(s);
+  return (d == 0.0) || (a.B64[q] > __dmul_rn(a.theta64, d));
+}
+
+// Coordinates for decisions on beams that lie in a plane of constant x[c]
+// (a zero beam component): half-open boxes [lo, hi) hold the beam iff
+// lo <= x[c] < hi, decided as on the FP64 position.  Box faces are
+// multiples of 2^-21, exact in FP32, and rounding to nearest never carries a
+// coordinate across one; the FP32 value only disagrees when it lands on a
+// face that the FP64 value lies just below, and then the next float below
+// restores the FP64 answer.
+__device__ __forceinline__ float3 grazing_coords(const WalkArgs& a, int si, float3 x) {
+  const double* p = a.pos64 + 3 * int64_t(si);
+  float g[3] = {x.x, x.y, x.z};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double f = double(g[c]) * 2097152.0;
+    if (f == floor(f) && p[c] < double(g[c])) g[c] = nextafterf(g[c], -INFINITY);
+  }
+  return make_float3(g[0], g[1], g[2]);
+}
+
+// Sec. 2.5.2: open iff d == 0 or B > theta d.
+__device__ __forceinline__ bool cell_opens(const WalkArgs& a, int q, const NodeW& nd, float3 x,
+                                           int si) {
+  const float3 e = node_ext(nd.meta);
+  const float dx = fmaxf(0.0f, fmaxf(nd.lo[0] - x.x, x.x - (nd.lo[0] + e.x)));
+  const float dy = fmaxf(0.0f, fmaxf(nd.lo[1] - x.y, x.y - (nd.lo[1] + e.y)));
+  const float dz = fmaxf(0.0f, fmaxf(nd.lo[2] - x.z, x.z - (nd.lo[2] + e.z)));
+  const float d2 = dx * dx + dy * dy + dz * dz;
+  if (d2 == 0.0f) return true;
+  const float B = nd.B;
+  const float margin = B * B - a.theta2 * d2;
+  const float g = 2.2f * B * (a.guard_abs + a.guard_rel * B);
+  if (fabsf(margin) > g) return margin > 0.0f;
+  return opens64(a, q, nd, si);
+}
+
+// Eq. intint as a kernel of r for an element of size h (normalised units).
+static __device__ float soft_kernel(float r, float h) {
+  const float x = r / (0.48860251190292f * h);
+  float g;
+  if (x == 1.0f) {
+    g = 0.5f;
+  } else if (x <= 2.0f) {
+    const float xm = x - 1.0f, xp = x + 1.0f;
+    g = 0.5f * (1.0f + (x * x - 1.0f) / (4.0f * x) * logf((xm * xm) / (xp * xp)));
+  } else {
+    // sum_{m>=1} x^{-2m}/(4m^2-1): the same function without the cancellation
+    const float ix2 = 1.0f / (x * x);
+    float xm = 1.0f, s = 0.0f;
+    for (int m = 1; m < 64; ++m) {
+      xm *= ix2;
+      const float term = xm / float(4 * m * m - 1);
+      s += term;
+      if (term < 1e-9f * s) break;
+    }
+    g = s;
+  }
+  return g / (h * h);
+}
+
+// Bin one source: beam, projected distance, r/s, kernel.  Returns false for
+// a source on top of the receiver (r == 0) or with s <= 0.
+__device__ __forceinline__ bool make_source(const WalkArgs& a, float3 p, const double* p64,
+                                            float3 x, int si, int ref, SrcEntry& out, int& pix) {
+  const float vx = p.x - x.x, vy = p.y - x.y, vz = p.z - x.z;
+  const float r2 = vx * vx + vy * vy + vz * vz;
+  if (!(r2 > 0.0f)) return false;
+  const float r = sqrtf(r2);
+  int k = hp_vec2pix_f32(a.nside, vx, vy, vz, hp_guard(a.nside, r));
+  if (k < 0) {
+    const double* x64 = a.pos64 + 3 * int64_t(si);
+    k = hp_vec2pix_f64(a.nside, __dsub_rn(p64[0], x64[0]), __dsub_rn(p64[1], x64[1]),
+                       __dsub_rn(p64[2], x64[2]));
+  }
+  const float4 n = a.dirs[k];
+  const float s = vx * n.x + vy * n.y + vz * n.z;
+  if (!(s > 0.0f)) return false;
+  out.s = s;
+  out.rs = r / s;
+  out.w = (a.flags & TREVR2_SOFT) ? soft_kernel(r, a.hn[si]) : 1.0f / (kFourPi * r2);
+  out.ref = ref;
+  pix = k;
+  return true;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// Phase S for the sources whose running index is in [lo, lo + M).  Returns
+// the total number of sources of this receiver (warp-uniform).
+static __device__ int phase_sources(const WalkArgs& a, float3 x, int si, int lane, int* stk, int cap,
+                             SrcEntry* U, int* Up, int lo) {
+  int sp = 1;
+  if (lane == 0) stk[0] = 0;
+  __syncwarp();
+  int emitted = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  while (sp > 0) {
+    const int k = min(32, sp);
+    const int q = lane < k ? stk[sp - 1 - lane] : -1;
+    sp -= k;
+    __syncwarp();
+    int npush = 0, child = -1, leaf_first = 0, leaf_count = 0;
+    bool emit_node = false;
+    SrcEntry ent;
+    int pix = 0;
+    if (q >= 0) {
+      const NodeW nd = a.nodes[q];
+      if (nd.meta & kMetaHasL) {
+        if (!cell_opens(a, q, nd, x, si)) {
+          const float4 c = a.csrc[q];
+          emit_node = make_source(a, make_float3(c.x, c.y, c.z), a.c64 + 3 * int64_t(q), x, si, q,
+                                  ent, pix);
+        } else if (nd.meta & kMetaLeaf) {
+          leaf_first = nd.aux;
+          leaf_count = nd.count;
+        } else {
+          npush = 2;
+          child = nd.child;
+        }
+      }
+    }
+    // push opened halves
+    const int incl = warp_incl_scan(npush, lane);
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    if (npush) {
+      const int pos = sp + incl - npush;
+      if (pos + 2 <= cap) {
+        stk[pos] = child + 1;
+        stk[pos + 1] = child;
+      } else {
+        atomicOr(a.status, kStatusStackOverflow);
+      }
+    }
+    sp = min(sp + tot, cap);
+    // accepted luminous cells
+    {
+      const unsigned m = __ballot_sync(0xffffffffu, emit_node);
+      const int idx = emitted + __popc(m & lt) - lo;
+      if (emit_node && idx >= 0 && idx < a.M) {
+        U[idx] = ent;
+        Up[idx] = pix;
+      }
+      emitted += __popc(m);
+    }
+    // luminous elements of opened leaves
+    int maxc = leaf_count;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxc = max(maxc, __shfl_xor_sync(0xffffffffu, maxc, o));
+    for (int e = 0; e < maxc; ++e) {
+      bool em = false;
+      if (e < leaf_count) {
+        const int sj = leaf_first + e;
+        const float4 pj = a.pos32[sj];
+        if (pj.w > 0.0f && sj != si)
+          em = make_source(a, make_float3(pj.x, pj.y, pj.z), a.pos64 + 3 * int64_t(sj), x, si,
+                           sj | kRefElement, ent, pix);
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, em);
+      const int idx = emitted + __popc(m & lt) - lo;
+      if (em && idx >= 0 && idx < a.M) {
+        U[idx] = ent;
+        Up[idx] = pix;
+      }
+      emitted += __popc(m);
+    }
+    __syncwarp();
+  }
+  return emitted;
+}
+
+// Bucket the n sources of U by beam into V; off[k] ends as the end of
+// bucket k (its start is off[k-1], or 0).  Each bucket is sorted by s.
+static __device__ void bin_sources(const WalkArgs& a, int lane, const SrcEntry* U, const int* Up, int n,
+                            SrcEntry* V, int* off) {
+  const int npix = a.npix;
+  for (int k = lane; k < npix; k += 32) off[k] = 0;
+  __syncwarp();
+  for (int e = lane; e < n; e += 32) atomicAdd(&off[Up[e]], 1);
+  __syncwarp();
+  // exclusive scan of the bucket sizes
+  const int per = (npix + 31) / 32;
+  const int b0 = min(lane * per, npix), b1 = min(b0 + per, npix);
+  int sum = 0;
+  for (int k = b0; k < b1; ++k) sum += off[k];
+  const int incl = warp_incl_scan(sum, lane);
+  int run = incl - sum;
+  for (int k = b0; k < b1; ++k) {
+    const int c = off[k];
+    off[k] = run;
+    run += c;
+  }
+  __syncwarp();
+  for (int e = lane; e < n; e += 32) {
+    const int slot = atomicAdd(&off[Up[e]], 1);
+    V[slot] = U[e];
+  }
+  __syncwarp();
+  // insertion sort of each bucket by projected distance
+  for (int k = lane; k < npix; k += 32) {
+    const int s0 = k ? off[k - 1] : 0, s1 = off[k];
+    for (int i = s0 + 1; i < s1; ++i) {
+      const SrcEntry v = V[i];
+      int j = i - 1;
+      while (j >= s0 && V[j].s > v.s) {
+        V[j + 1] = V[j];
+        --j;
+      }
+      V[j + 1] = v;
+    }
+  }
+  __syncwarp();
+}
+
+template <int NBP>
+struct BandVec {
+  float v[NBP];
+};
+
+template <int NBP>
+__device__ __forceinline__ BandVec<NBP> load_bands(const float* p) {
+  BandVec<NBP> r;
+  if constexpr (NBP == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+  } else if constexpr (NBP == 2) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    r.v[0] = t.x; r.v[1] = t.y;
+  } else {
+    r.v[0] = *p;
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Host side (walk.cu).
+bool valid_nside(int nside);
+// Per-tree walk arguments for one nside (everything but the receivers, the
+// output and the buffers).
+void fill_walk_args(const Tree* t, const Table* tb, int nside, float theta, const int* bsel,
+                    int nbsel, uint32_t flags, int M, WalkArgs* a);
+// Shared memory attribute and resident blocks per SM of a walk kernel.
+int config_walk_kernel(const void* fn, int warps, size_t smem, int* per_sm, int* sms);
+// Synchronises `st` and returns (and clears) the tree's device status.
+int read_status(Tree* t, cudaStream_t st);
+
+// Per-warp shared memory of a walk block: the traversal stacks, the beam
+// bucket offsets and the next-beam counter.
+inline size_t walk_smem(int warps, int stack_ints, int npix) {
+  return size_t(warps) * (stack_ints + npix + 1) * sizeof(int);
+}
+
+}  // namespace trevr2
