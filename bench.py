@@ -325,6 +325,9 @@ def run_ours(args, world, rank, local):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if world == 1 and not args.no_adjoint:
+        line["adjoint"] = run_adjoint(args, dev)
+        line["adjoint_forward_ratio"] = line["adjoint"]["ratio"]
     if world == 1 and not args.no_batched:
         per_rec = roofline["algorithmic_bytes_per_unit"] * npix * nb if roofline else None
         line["batched"] = run_batched(args, dev, per_rec, hbm_peak, peak_kind)
@@ -428,6 +431,53 @@ def run_batched(args, dev, per_receiver_bytes, hbm_peak, peak_kind):
     return out
 
 
+def run_adjoint(args, dev):
+    """Adjoint cost: the 64^3 lognormal field (sigma 1), 1024 sources, 2 bands,
+    nside 2, theta 0.75, every gas element a receiver, Loss = sum_i w_i J_i
+    with w ~ U(0,1).  Forward = the J walk; backward = trevr2_J_backward
+    (adjoint walk, table adjoint, element sums); tree and tables are built
+    once before timing."""
+    import torch
+
+    import paper_2310_15235_gb300 as t2
+
+    case = workloads.adjoint_case()
+    nside, theta = case["nside"], case["theta"]
+    d = {k: torch.from_numpy(np.ascontiguousarray(case[k])).to(dev)
+         for k in ("pos", "mass", "kappa", "lum", "h", "active")}
+    tree = t2.build(d["pos"], d["mass"], d["kappa"], d["lum"], d["h"], case["box_lo"],
+                    case["box_size"], case["bucket"], device=dev)
+    tree.prepare(nside)
+    A, nb = len(case["active"]), case["nb"]
+    w = torch.rand((A, nb), device=dev, generator=torch.Generator(dev).manual_seed(5))
+    J = torch.empty((A, nb), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    reps = 3
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tree.status()
+        return e0.elapsed_time(e1) / reps
+
+    fwd = timed(lambda: tree.J(d["active"], nside, theta, out=J, flags=t2.ASYNC))
+    bwd = timed(lambda: tree.J_backward(d["active"], w, nside, theta, flags=t2.ASYNC))
+    units = A * 12 * nside ** 2 * nb
+    tree.free()
+    return {"workload": "64^3 lognormal gas (sigma 1.0) + 1024 sources, 2 bands, nside 2, "
+                        "theta 0.75, all 262,144 gas receivers, Loss = sum_i w_i J_i",
+            "forward_ms": fwd, "backward_ms": bwd, "ratio": bwd / fwd,
+            "forward_units_per_s": units / (fwd * 1e-3),
+            "backward_units_per_s": units / (bwd * 1e-3)}
+
+
 def run_walk_only(args):
     """The walk kernel alone on a clumpy field of lattice^3 gas (profiling
     aid): tree and tables built once, then `warmup + steps` walks."""
@@ -478,6 +528,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the individual-timestep batching measurement")
     ap.add_argument("--batched-reps", type=int, default=2)
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint / forward timing")
     args = ap.parse_args()
     if args.walk_only:
         run_walk_only(args)

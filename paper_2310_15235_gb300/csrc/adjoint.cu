@@ -104,13 +104,15 @@ __device__ __forceinline__ double thick_factor_deriv(double tau) {
   return (exp(-tau) * (1.0 + tau) - 1.0) / (tau * tau);
 }
 
-// Chord of beam (x, n) with the box of node nd, clipped to [0, tmax].
+// Chord of beam (x, n) with the box of node nd, clipped to [0, tmax]; tx is
+// the exit before the clip at tmax.
 __device__ __forceinline__ bool beam_chord(const NodeW& nd, const float xv[3], const float n[3],
-                                           const float inv[3], float tmax, float& t0, float& t1) {
+                                           const float inv[3], float tmax, float& t0, float& t1,
+                                           float& tx) {
   const float3 e = node_ext(nd.meta);
   const float ext[3] = {e.x, e.y, e.z};
   t0 = 0.0f;
-  t1 = tmax;
+  tx = INFINITY;
   bool hit = true;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -120,19 +122,21 @@ __device__ __forceinline__ bool beam_chord(const NodeW& nd, const float xv[3], c
     } else {
       const float ta = (lo - xv[c]) * inv[c], tb = (hi - xv[c]) * inv[c];
       t0 = fmaxf(t0, fminf(ta, tb));
-      t1 = fminf(t1, fmaxf(ta, tb));
+      tx = fminf(tx, fmaxf(ta, tb));
     }
   }
+  t1 = fminf(tmax, tx);
   return hit && (t0 < t1);
 }
 
 // One source seen front to back: its term of J, dLoss/dL, dLoss/dc and q.
+// tau_k(s) = tau + al ds; as_ is the absorption at s (dtau_k/ds).
 template <int NBP>
 __device__ __forceinline__ void source_adjoint(const AdjArgs& g, const SrcEntry& src, float3 x,
                                                const float n[3], const float* tau,
-                                               const BandVec<NBP>& al, float ds, bool inside,
-                                               float* Qrow, const float* gJf, float* Js,
-                                               float* Jc, float hr) {
+                                               const BandVec<NBP>& al, float ds,
+                                               const BandVec<NBP>& as_, float* Qrow,
+                                               const float* gJf, float* Js, float* Jc, float hr) {
   const WalkArgs& a = g.w;
   const bool elem = (src.ref & kRefElement) != 0;
   const int64_t idx = src.ref & 0x7fffffff;
@@ -162,9 +166,8 @@ __device__ __forceinline__ void source_adjoint(const AdjArgs& g, const SrcEntry&
     float fr = 0.0f, fn = 0.0f;  // coefficients of rhat and n
 #pragma unroll
     for (int b = 0; b < NBP; ++b) {
-      const float as = inside ? al.v[b] : 0.0f;
       fr += cb[b] * (dlg - tk[b] / src.s);
-      fn += cb[b] * src.rs * (tk[b] / src.s - as);
+      fn += cb[b] * src.rs * (tk[b] / src.s - as_.v[b]);
     }
     if (fr != 0.0f || fn != 0.0f) {
       float* gc = g.g_c + 3 * idx;
@@ -199,9 +202,16 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
     for (int c = 0; c < 3; ++c) inv[c] = n[c] != 0.0f ? 1.0f / n[c] : 0.0f;
 
     // front to back: tau at every source
+    BandVec<NBP> zero;
+#pragma unroll
+    for (int b = 0; b < NBP; ++b) zero.v[b] = 0.0f;
     float tau[NBP];
 #pragma unroll
     for (int b = 0; b < NBP; ++b) tau[b] = 0.0f;
+    // the last absorbing segment: its start, unclipped exit and alpha (the
+    // farthest sources lie in it when it was clipped at smax)
+    float seg_t0 = 0.0f, seg_x = 0.0f;
+    BandVec<NBP> seg_al = zero;
     int ptr = start;
     int sp = 1;
     lstk[0] = 0;
@@ -209,8 +219,8 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
       const int q = lstk[--sp];
       const NodeW nd = a.nodes[q];
       if (!(nd.meta & kMetaHasAlpha)) continue;
-      float t0, t1;
-      if (!beam_chord(nd, xv, n, inv, smax, t0, t1)) continue;
+      float t0, t1, tx;
+      if (!beam_chord(nd, xv, n, inv, smax, t0, t1, tx)) continue;
       if (!(nd.meta & kMetaLeaf) && cell_opens(a, q, nd, x, si)) {
         const int axis = int(nd.meta & kMetaDepthMask) % 3;
         const float3 e = node_ext(nd.meta);
@@ -228,20 +238,21 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
       while (ptr < end) {
         const SrcEntry src = V[ptr];
         if (!(src.s < t1)) break;
-        source_adjoint<NBP>(g, src, x, n, tau, al, fmaxf(0.0f, src.s - t0), src.s > t0,
-                            Q + int64_t(ptr) * NBP, gJf, Js, Jc, hr);
+        source_adjoint<NBP>(g, src, x, n, tau, al, fmaxf(0.0f, src.s - t0),
+                            src.s > t0 ? al : zero, Q + int64_t(ptr) * NBP, gJf, Js, Jc, hr);
         ++ptr;
       }
 #pragma unroll
       for (int b = 0; b < NBP; ++b) tau[b] += al.v[b] * (t1 - t0);
+      seg_t0 = t0;
+      seg_x = tx;
+      seg_al = al;
     }
-    {
-      BandVec<NBP> zero;
-#pragma unroll
-      for (int b = 0; b < NBP; ++b) zero.v[b] = 0.0f;
-      for (; ptr < end; ++ptr)
-        source_adjoint<NBP>(g, V[ptr], x, n, tau, zero, 0.0f, false, Q + int64_t(ptr) * NBP, gJf,
-                            Js, Jc, hr);
+    for (; ptr < end; ++ptr) {
+      const SrcEntry src = V[ptr];
+      const bool in_seg = src.s > seg_t0 && src.s < seg_x;
+      source_adjoint<NBP>(g, src, x, n, tau, zero, 0.0f, in_seg ? seg_al : zero,
+                          Q + int64_t(ptr) * NBP, gJf, Js, Jc, hr);
     }
 
     // back to front: the absorption gradient of every segment
@@ -255,8 +266,8 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
       const int q = lstk[--sp];
       const NodeW nd = a.nodes[q];
       if (!(nd.meta & kMetaHasAlpha)) continue;
-      float t0, t1;
-      if (!beam_chord(nd, xv, n, inv, smax, t0, t1)) continue;
+      float t0, t1, tx;
+      if (!beam_chord(nd, xv, n, inv, smax, t0, t1, tx)) continue;
       if (!(nd.meta & kMetaLeaf) && cell_opens(a, q, nd, x, si)) {
         // far half on top of the stack
         const int axis = int(nd.meta & kMetaDepthMask) % 3;

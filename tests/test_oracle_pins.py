@@ -562,3 +562,39 @@ def test_dual_derivative_matches_central_difference(oracle_mod):
         fd = (vals[0] - vals[1]) / (2 * step)
         scale = np.abs(fd).max() + 1e-300
         assert np.abs(dJ - fd).max() <= 1e-5 * scale, (which, elem, band)
+
+
+@pytest.mark.parametrize("flags", [0, 3])
+def test_dual_loss_gradient_matches_central_difference_64(oracle_mod, flags):
+    """The adjoint workload's loss sum_i w_i J_i (w ~ U(0,1)) on a 16^3
+    version of its field: the dual-number gradient for 64 random parameters
+    (32 kappa of gas, 32 L of sources) equals FP64 central differences with
+    a relative step of 1e-6."""
+    case = workloads.adjoint_case(n=16, n_src=64)
+    nside, theta = case["nside"], case["theta"]
+    rng = np.random.default_rng(21)
+    act = np.sort(rng.choice(case["active"], 256, replace=False))
+    w = rng.uniform(0.0, 1.0, size=(len(act), case["nb"]))
+    t = oracle_mod.OracleTree.from_case(case)
+    n_gas = int((case["mass"] > 0).sum())
+    src = np.flatnonzero(case["lum"].sum(1) > 0)
+    params = [("kappa", int(e), int(rng.integers(0, 2))) for e in rng.choice(n_gas, 32, False)]
+    params += [("lum", int(e), int(rng.integers(0, 2))) for e in rng.choice(src, 32, False)]
+    dual, fd = [], []
+    for which, elem, band in params:
+        dual.append(float((t.J_deriv(act, nside, theta, which, elem, band, flags) * w).sum()))
+        base = float(case[which][elem, band])
+        step = 1e-6 * base
+        vals = []
+        for sgn in (+1, -1):
+            c2 = dict(case)
+            a2 = case[which].astype(np.float64).copy()
+            a2[elem, band] = base + sgn * step
+            c2[which] = a2
+            vals.append(float((oracle_mod.OracleTree.from_case(c2).J(act, nside, theta, flags)
+                               * w).sum()))
+        fd.append((vals[0] - vals[1]) / (2 * step))
+    dual, fd = np.array(dual), np.array(fd)
+    scale = np.abs(fd).max()
+    assert scale > 0
+    np.testing.assert_allclose(dual, fd, rtol=1e-5, atol=1e-7 * scale)
