@@ -19,8 +19,10 @@
 //       dLoss/dc_src    += sum_b c_b [ (w'/w) rhat - dtau_b/dc ]  (cells only),
 //       dtau/dc = (r/s) alpha(s) n + (tau_k(s)/s) (rhat - (r/s) n),
 //     with c_b = gJ_ib F_ib L_b w e^{-tau_b}, and keeps q_b = c_b r/s per
-//     source.  Back to front it carries W_b = sum of q_b over the sources
-//     beyond the current segment [t0, t1) and adds to the segment's cell
+//     source, and records the beam's segments.  Back to front (over the
+//     recorded segments, or walking the beam again far half first when it
+//     had more than the record holds) it carries W_b = sum of q_b over the
+//     sources beyond the current segment [t0, t1) and adds to the cell
 //       dLoss/dalpha_b -= W_b (t1 - t0) + sum_{t0 <= s < t1} q_b (s - t0),
 //     so every segment costs O(1) however many sources lie past it.
 //  2. tables, top down: dalpha_parent/dalpha_half from Eq. transmissionavg,
@@ -33,6 +35,7 @@
 //     dc/dL_e = (x_e - c)/L_tot, and adds e's own term as a point source.
 #include <cfloat>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 
 #include "walk.cuh"
@@ -51,7 +54,47 @@ struct AdjArgs {
   float* g_Lelem;    // [N][NBP] dLoss/dL of elements as point sources (sorted order)
   float* g_thick;    // [N][NBP] Eq. taucorr's dLoss/dkappa (sorted order)
   float* Q;          // [warps][M][NBP] q_b = c_b r/s per staged source
+  float4* seg;       // [warps][seg_cap][32] per lane: segment target, t0, t1
+  int seg_cap;       // segments recorded per lane and beam (0: always re-walk)
 };
+
+// Segments of one beam recorded front to back, replayed back to front.
+constexpr int kSegCap = 64;
+constexpr int kAdjWarps = 8;  // warps per block of the adjoint walk
+
+// The absorption gradient of one segment [t0, t1) of a beam (back to front):
+// W holds sum q over the sources beyond t1, p2 the nearest source not yet
+// passed.
+template <int NBP>
+__device__ __forceinline__ void segment_gradient(float* __restrict__ dst, float t0, float t1,
+                                                 const SrcEntry* V, const float* Q, int start,
+                                                 int& p2, float* W) {
+  while (p2 >= start && !(V[p2].s < t1)) {
+    const BandVec<NBP> qv = load_bands<NBP>(Q + int64_t(p2) * NBP);
+#pragma unroll
+    for (int b = 0; b < NBP; ++b) W[b] += qv.v[b];
+    --p2;
+  }
+  float gin[NBP], win[NBP];
+#pragma unroll
+  for (int b = 0; b < NBP; ++b) gin[b] = win[b] = 0.0f;
+  while (p2 >= start && V[p2].s >= t0) {
+    const float ds = V[p2].s - t0;
+    const BandVec<NBP> qv = load_bands<NBP>(Q + int64_t(p2) * NBP);
+#pragma unroll
+    for (int b = 0; b < NBP; ++b) {
+      gin[b] += qv.v[b] * ds;
+      win[b] += qv.v[b];
+    }
+    --p2;
+  }
+#pragma unroll
+  for (int b = 0; b < NBP; ++b) {
+    const float ga = -(W[b] * (t1 - t0) + gin[b]);
+    if (ga != 0.0f) atomicAdd(dst + b, ga);
+    W[b] += win[b];
+  }
+}
 
 // d ln g / dr of Eq. intint's kernel g(r) = G(x)/h^2, x = r/(0.4886 h).
 // G(x) = 1 - sum_m x^{2m}/(4m^2-1) for x < 1 and sum_m x^{-2m}/(4m^2-1) for
@@ -182,8 +225,8 @@ __device__ __forceinline__ void source_adjoint(const AdjArgs& g, const SrcEntry&
 // back to front (see the file comment).
 template <int NBP>
 __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int* lstk,
-                               const SrcEntry* V, float* Q, const int* off, int* next_beam,
-                               const float* gJf, float* Js, float* Jc) {
+                               const SrcEntry* V, float* Q, float4* S, const int* off,
+                               int* next_beam, const float* gJf, float* Js, float* Jc) {
   const WalkArgs& a = g.w;
   const float hr = a.hn[si];
   const float xv[3] = {x.x, x.y, x.z};
@@ -212,6 +255,7 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
     // farthest sources lie in it when it was clipped at smax)
     float seg_t0 = 0.0f, seg_x = 0.0f;
     BandVec<NBP> seg_al = zero;
+    int nseg = 0;
     int ptr = start;
     int sp = 1;
     lstk[0] = 0;
@@ -222,11 +266,7 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
       float t0, t1, tx;
       if (!beam_chord(nd, xv, n, inv, smax, t0, t1, tx)) continue;
       if (!(nd.meta & kMetaLeaf) && cell_opens(a, q, nd, x, si)) {
-        const int axis = int(nd.meta & kMetaDepthMask) % 3;
-        const float3 e = node_ext(nd.meta);
-        const float ext[3] = {e.x, e.y, e.z};
-        const float mid = nd.lo[axis] + 0.5f * ext[axis];
-        const bool lower_first = xv[axis] < mid;
+        const bool lower_first = in_lower_half(nd, xv);
         lstk[sp] = lower_first ? nd.child + 1 : nd.child;
         lstk[sp + 1] = lower_first ? nd.child : nd.child + 1;
         sp += 2;
@@ -235,6 +275,11 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
       const BandVec<NBP> al =
           (nd.meta & kMetaLeaf) ? load_bands<NBP>(a.alpha_leaf + int64_t(q) * NBP)
                                 : load_bands<NBP>(a.alpha_tab + (int64_t(nd.aux) * a.P + pair) * NBP);
+      if (nseg < g.seg_cap) {
+        const int dst = (nd.meta & kMetaLeaf) ? -(q + 1) : nd.aux * a.P + pair;
+        S[nseg * 32 + lane] = make_float4(__int_as_float(dst), t0, t1, 0.0f);
+      }
+      ++nseg;
       while (ptr < end) {
         const SrcEntry src = V[ptr];
         if (!(src.s < t1)) break;
@@ -255,57 +300,40 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
                           Q + int64_t(ptr) * NBP, gJf, Js, Jc, hr);
     }
 
-    // back to front: the absorption gradient of every segment
+    // back to front: the absorption gradient of every segment, from the
+    // recorded segments or, when a beam had more, by walking it again with
+    // the far half first
     float W[NBP];
 #pragma unroll
     for (int b = 0; b < NBP; ++b) W[b] = 0.0f;
     int p2 = end - 1;
-    sp = 1;
-    lstk[0] = 0;
-    while (sp > 0) {
-      const int q = lstk[--sp];
-      const NodeW nd = a.nodes[q];
-      if (!(nd.meta & kMetaHasAlpha)) continue;
-      float t0, t1, tx;
-      if (!beam_chord(nd, xv, n, inv, smax, t0, t1, tx)) continue;
-      if (!(nd.meta & kMetaLeaf) && cell_opens(a, q, nd, x, si)) {
-        // far half on top of the stack
-        const int axis = int(nd.meta & kMetaDepthMask) % 3;
-        const float3 e = node_ext(nd.meta);
-        const float ext[3] = {e.x, e.y, e.z};
-        const float mid = nd.lo[axis] + 0.5f * ext[axis];
-        const bool lower_first = xv[axis] < mid;
-        lstk[sp] = lower_first ? nd.child : nd.child + 1;
-        lstk[sp + 1] = lower_first ? nd.child + 1 : nd.child;
-        sp += 2;
-        continue;
+    if (nseg <= g.seg_cap) {
+      for (int j = nseg - 1; j >= 0; --j) {
+        const float4 r = S[j * 32 + lane];
+        const int dst = __float_as_int(r.x);
+        float* d = dst < 0 ? g.g_aleaf + int64_t(-dst - 1) * NBP : g.g_atab + int64_t(dst) * NBP;
+        segment_gradient<NBP>(d, r.y, r.z, V, Q, start, p2, W);
       }
-      while (p2 >= start && !(V[p2].s < t1)) {
-        const BandVec<NBP> qv = load_bands<NBP>(Q + int64_t(p2) * NBP);
-#pragma unroll
-        for (int b = 0; b < NBP; ++b) W[b] += qv.v[b];
-        --p2;
-      }
-      float gin[NBP], win[NBP];
-#pragma unroll
-      for (int b = 0; b < NBP; ++b) gin[b] = win[b] = 0.0f;
-      while (p2 >= start && V[p2].s >= t0) {
-        const float ds = V[p2].s - t0;
-        const BandVec<NBP> qv = load_bands<NBP>(Q + int64_t(p2) * NBP);
-#pragma unroll
-        for (int b = 0; b < NBP; ++b) {
-          gin[b] += qv.v[b] * ds;
-          win[b] += qv.v[b];
+    } else {
+      sp = 1;
+      lstk[0] = 0;
+      while (sp > 0) {
+        const int q = lstk[--sp];
+        const NodeW nd = a.nodes[q];
+        if (!(nd.meta & kMetaHasAlpha)) continue;
+        float t0, t1, tx;
+        if (!beam_chord(nd, xv, n, inv, smax, t0, t1, tx)) continue;
+        if (!(nd.meta & kMetaLeaf) && cell_opens(a, q, nd, x, si)) {
+          // far half on top of the stack
+          const bool lower_first = in_lower_half(nd, xv);
+          lstk[sp] = lower_first ? nd.child : nd.child + 1;
+          lstk[sp + 1] = lower_first ? nd.child + 1 : nd.child;
+          sp += 2;
+          continue;
         }
-        --p2;
-      }
-      float* dst = (nd.meta & kMetaLeaf) ? g.g_aleaf + int64_t(q) * NBP
+        float* d = (nd.meta & kMetaLeaf) ? g.g_aleaf + int64_t(q) * NBP
                                          : g.g_atab + (int64_t(nd.aux) * a.P + pair) * NBP;
-#pragma unroll
-      for (int b = 0; b < NBP; ++b) {
-        const float ga = -(W[b] * (t1 - t0) + gin[b]);
-        if (ga != 0.0f) atomicAdd(dst + b, ga);
-        W[b] += win[b];
+        segment_gradient<NBP>(d, t0, t1, V, Q, start, p2, W);
       }
     }
     k = atomicAdd(next_beam, 1);
@@ -315,7 +343,7 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
 template <int NBP>
 __device__ __forceinline__ void adjoint_receiver(const AdjArgs& g, int64_t slot, int lane, int* stk,
                                                  int* off, int* next_beam, int* lstk, SrcEntry* U,
-                                                 int* Up, SrcEntry* V, float* Q) {
+                                                 int* Up, SrcEntry* V, float* Q, float4* S) {
   const WalkArgs& a = g.w;
   const int64_t io = a.active[slot];
   if (io < 0 || io >= a.N) {
@@ -357,7 +385,7 @@ __device__ __forceinline__ void adjoint_receiver(const AdjArgs& g, int64_t slot,
       bin_sources(a, lane, U, Up, n, V, off);
       if (lane == 0) *next_beam = 32;
       __syncwarp();
-      absorb_adjoint<NBP>(g, x, si, lane, lstk, V, Q, off, next_beam, gJf, Js, Jc);
+      absorb_adjoint<NBP>(g, x, si, lane, lstk, V, Q, S, off, next_beam, gJf, Js, Jc);
       __syncwarp();
     }
     if (lo + a.M >= total) break;
@@ -393,12 +421,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_walk_adjoint(const __grid_consta
   int* Up = a.pixU + gw * a.M;
   SrcEntry* V = a.srcV + gw * a.M;
   float* Q = g.Q + gw * a.M * NBP;
+  float4* S = g.seg + gw * g.seg_cap * 32;
   for (;;) {
     unsigned long long slot = 0;
     if (lane == 0) slot = atomicAdd(a.counter, 1ull);
     slot = __shfl_sync(0xffffffffu, slot, 0);
     if (slot >= (unsigned long long)a.A) break;
-    adjoint_receiver<NBP>(g, int64_t(slot), lane, stk, off, next_beam, lstk, U, Up, V, Q);
+    adjoint_receiver<NBP>(g, int64_t(slot), lane, stk, off, next_beam, lstk, U, Up, V, Q, S);
   }
 }
 
@@ -506,7 +535,7 @@ __global__ void k_grad_elements(int64_t N, int nb, double inv_size2, const int* 
 
 template <int NBP>
 const void* adjoint_kernel() {
-  return reinterpret_cast<const void*>(&k_walk_adjoint<NBP, kWalkWarps>);
+  return reinterpret_cast<const void*>(&k_walk_adjoint<NBP, kAdjWarps>);
 }
 
 }  // namespace
@@ -573,12 +602,12 @@ extern "C" int trevr2_J_backward(trevr2_tree* tree, const int64_t* active, int64
   wa.A = A;
   wa.active = active;
   const void* fn = nbp == 1 ? adjoint_kernel<1>() : nbp == 2 ? adjoint_kernel<2>() : adjoint_kernel<4>();
-  const size_t smem = walk_smem(kWalkWarps, wa.stack_ints, wa.npix);
+  const size_t smem = walk_smem(kAdjWarps, wa.stack_ints, wa.npix);
   int per_sm = 0, sms = 0;
-  T2_CHECK(config_walk_kernel(fn, kWalkWarps, smem, &per_sm, &sms));
+  T2_CHECK(config_walk_kernel(fn, kAdjWarps, smem, &per_sm, &sms));
   int64_t blocks = int64_t(sms) * per_sm;
-  blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (A + kWalkWarps - 1) / kWalkWarps));
-  const size_t warps = size_t(blocks) * kWalkWarps;
+  blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (A + kAdjWarps - 1) / kAdjWarps));
+  const size_t warps = size_t(blocks) * kAdjWarps;
 
   // one allocation: gradient buffers (zeroed), leaf map, walk buffers
   auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
@@ -591,10 +620,14 @@ extern "C" int trevr2_J_backward(trevr2_tree* tree, const int64_t* active, int64
   const size_t zeroed = b_atab + b_aleaf + b_Lnode + b_c + b_Lelem + b_thick;
   const size_t b_leaf = up(sizeof(int) * size_t(std::max<int64_t>(N, 1)));
   const size_t b_Q = up(sizeof(float) * warps * wa.M * nbp);
+  // segment records address the table by a 32-bit row index
+  const int seg_cap = int64_t(std::max<int64_t>(t->n_internal, 1)) * P < INT32_MAX ? kSegCap : 0;
+  const size_t b_seg = up(sizeof(float4) * warps * size_t(seg_cap) * 32);
   const size_t b_walk = warps * size_t(wa.M) * (2 * sizeof(SrcEntry) + sizeof(int));
   char* base = nullptr;
   {
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), zeroed + b_leaf + b_Q + b_walk, st);
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base),
+                                    zeroed + b_leaf + b_Q + b_seg + b_walk, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(adjoint buffers)");
   }
   AdjArgs g;
@@ -610,6 +643,8 @@ extern "C" int trevr2_J_backward(trevr2_tree* tree, const int64_t* active, int64
   g.g_thick = reinterpret_cast<float*>(p); p += b_thick;
   int* leaf_of = reinterpret_cast<int*>(p); p += b_leaf;
   g.Q = reinterpret_cast<float*>(p); p += b_Q;
+  g.seg = reinterpret_cast<float4*>(p); p += b_seg;
+  g.seg_cap = seg_cap;
   g.w.srcU = reinterpret_cast<SrcEntry*>(p);
   g.w.srcV = reinterpret_cast<SrcEntry*>(p + warps * wa.M * sizeof(SrcEntry));
   g.w.pixU = reinterpret_cast<int*>(p + 2 * warps * wa.M * sizeof(SrcEntry));
@@ -619,7 +654,7 @@ extern "C" int trevr2_J_backward(trevr2_tree* tree, const int64_t* active, int64
     if (A > 0) {
       T2_CUDA(cudaMemsetAsync(t->counter, 0, sizeof(unsigned long long), st));
       void* args[] = {&g};
-      T2_CUDA(cudaLaunchKernel(fn, dim3(unsigned(blocks)), dim3(kWalkWarps * 32), args, smem, st));
+      T2_CUDA(cudaLaunchKernel(fn, dim3(unsigned(blocks)), dim3(kAdjWarps * 32), args, smem, st));
       note_launch();
     }
     for (int d = 0; d < t->max_depth; ++d) {

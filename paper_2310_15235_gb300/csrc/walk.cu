@@ -82,9 +82,7 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
       if (!hit || !(t0 < t1)) continue;
       if (!(nd.meta & kMetaLeaf) && cell_opens(a, q, nd, x, si)) {
         // near half (the side of the receiver) on top of the stack
-        const int axis = int(nd.meta & kMetaDepthMask) % 3;
-        const float mid = nd.lo[axis] + 0.5f * ext[axis];
-        const bool lower_first = xv[axis] < mid;
+        const bool lower_first = in_lower_half(nd, xv);
         lstk[sp] = lower_first ? nd.child + 1 : nd.child;
         lstk[sp + 1] = lower_first ? nd.child : nd.child + 1;
         sp += 2;
@@ -191,7 +189,7 @@ __device__ __forceinline__ void walk_receiver(const WalkArgs& a, int64_t io, flo
 
 // One warp per receiver, receivers from a global counter.
 template <int NBP, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_walk(WalkArgs a) {
+__global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk(WalkArgs a) {
   extern __shared__ int smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;
@@ -239,7 +237,7 @@ struct BatchArgs {
 };
 
 template <int NBP, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_walk_batched(const __grid_constant__ BatchArgs B) {
+__global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk_batched(const __grid_constant__ BatchArgs B) {
   extern __shared__ int smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;

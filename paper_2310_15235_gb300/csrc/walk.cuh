@@ -12,7 +12,11 @@
 
 namespace trevr2 {
 
-constexpr int kWalkWarps = 8;                 // warps per block
+constexpr int kWalkWarps = 4;                 // warps per block
+// Resident warps per SM the walk kernels are compiled for: 7 blocks of 4
+// warps (72 registers a thread) measured faster than 6 at 80 registers and
+// than 8 at 64 registers, which spills.
+constexpr int kWalkWarpsPerSM = 28;
 constexpr int kSrcCapacity = 1024;            // sources held per warp and pass
 constexpr float kFourPi = 12.566370614359172f;
 
@@ -61,21 +65,35 @@ __device__ __forceinline__ float3 node_ext(uint32_t meta) {
                      __int_as_float((127 - splits_on_axis(d, 2)) << 23));
 }
 
-// FP64 opening decision, the definition evaluated without contraction.
-static __device__ __noinline__ bool opens64(const WalkArgs& a, int q, const NodeW& nd, int si) {
+// Whether x lies in the lower half of node nd along the node's split axis
+// (selects instead of an index, which would put the operands in local memory).
+__device__ __forceinline__ bool in_lower_half(const NodeW& nd, const float xv[3]) {
+  const int axis = int(nd.meta & kMetaDepthMask) % 3;
   const float3 e = node_ext(nd.meta);
+  const float lo = axis == 0 ? nd.lo[0] : (axis == 1 ? nd.lo[1] : nd.lo[2]);
+  const float ex = axis == 0 ? e.x : (axis == 1 ? e.y : e.z);
+  const float xa = axis == 0 ? xv[0] : (axis == 1 ? xv[1] : xv[2]);
+  return xa < lo + 0.5f * ex;
+}
+
+// FP64 opening decision, the definition evaluated without contraction.
+static __device__ __noinline__ bool opens64(const double* __restrict__ x64, double B,
+                                            double theta, float lx, float ly, float lz,
+                                            uint32_t meta) {
+  const float3 e = node_ext(meta);
   const double ext[3] = {double(e.x), double(e.y), double(e.z)};
+  const double lo3[3] = {double(lx), double(ly), double(lz)};
   double s = 0.0;
   for (int k = 0; k < 3; ++k) {
-    const double lo = double(nd.lo[k]), hi = __dadd_rn(lo, ext[k]);
-    const double x = a.pos64[3 * int64_t(si) + k];
+    const double lo = lo3[k], hi = __dadd_rn(lo, ext[k]);
+    const double x = x64[k];
     double dd = 0.0;
     if (x < lo) dd = __dsub_rn(lo, x);
     else if (x > hi) dd = __dsub_rn(x, hi);
     s = __dadd_rn(s, __dmul_rn(dd, dd));
   }
   const double d = sqrt(s);
-  return (d == 0.0) || (a.B64[q] > __dmul_rn(a.theta64, d));
+  return (d == 0.0) || (B > __dmul_rn(theta, d));
 }
 
 // Coordinates for decisions on beams that lie in a plane of constant x[c]
@@ -109,7 +127,8 @@ __device__ __forceinline__ bool cell_opens(const WalkArgs& a, int q, const NodeW
   const float margin = B * B - a.theta2 * d2;
   const float g = 2.2f * B * (a.guard_abs + a.guard_rel * B);
   if (fabsf(margin) > g) return margin > 0.0f;
-  return opens64(a, q, nd, si);
+  return opens64(a.pos64 + 3 * int64_t(si), a.B64[q], a.theta64, nd.lo[0], nd.lo[1], nd.lo[2],
+                 nd.meta);
 }
 
 // Eq. intint as a kernel of r for an element of size h (normalised units).

@@ -213,3 +213,42 @@ def test_backward_full_size_sampled(t2, oracle_mod, adjoint_field):
                         case["nside"], case["theta"], params)
     _check(_gather(gk, gl, params), want, "adjoint full size")
     tree.free()
+
+
+def _line_case(n=1500, nb=2, seed=58):
+    """Absorbing elements on a line along +x (a beam direction of nside 1)
+    with a source at its far end: with theta -> 0 every leaf on the line is
+    a segment of that beam (far more than the adjoint records per beam)."""
+    rng = np.random.default_rng(seed)
+    off = 0.5 + 1e-4
+    gas = np.stack([(np.arange(n) + 0.5) / n, np.full(n, off), np.full(n, off)], 1)
+    src = np.array([[0.9995, off, off], [0.3, 0.8, 0.2], [0.7, 0.1, 0.9]])
+    pos = np.concatenate([gas, src])
+    N = len(pos)
+    mass = np.concatenate([np.full(n, 1.0 / n), np.zeros(3)])
+    kappa = np.zeros((N, nb))
+    kappa[:n] = 2e-6 * rng.uniform(0.2, 1.0, size=(n, nb))  # tau ~ 1 along the line
+    lum = np.zeros((N, nb))
+    lum[n:] = rng.uniform(0.5, 1.0, size=(3, nb))
+    return dict(pos=pos, mass=mass, kappa=kappa, lum=lum, h=np.full(N, 1.0 / n),
+                active=np.arange(0, 40, 4, dtype=np.int64), nb=nb, nside=1, theta=1e-6,
+                box_lo=np.zeros(3), box_size=1.0, bucket=1, name="line")
+
+
+def test_backward_long_beam(t2, oracle_mod):
+    case = _line_case()
+    tree = _gpu_tree(t2, case)
+    act = case["active"]
+    ot = oracle_mod.OracleTree.from_case(case)
+    J = tree.J(act, 1, 1e-6).cpu().numpy()
+    ref, st = ot.J(act, 1, 1e-6, stats=True)
+    assert st[:, 2].min() > 1000  # segments per receiver
+    r = np.abs(J - ref) / np.abs(ref)
+    assert np.median(r) <= 1e-4 and r.max() <= 1e-3, r.max()
+    rng = np.random.default_rng(10)
+    gJ = rng.uniform(0.0, 1.0, size=(len(act), 2)).astype(np.float32)
+    gk, gl = tree.J_backward(act, gJ, 1, 1e-6)
+    params = _all_params(case, n_kappa=120, n_dark=10)
+    want = _oracle_grad(ot, act, gJ.astype(np.float64), 1, 1e-6, params)
+    _check(_gather(gk, gl, params), want, "long beam")
+    tree.free()
