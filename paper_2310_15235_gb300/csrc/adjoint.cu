@@ -266,10 +266,12 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
       float t0, t1, tx;
       if (!beam_chord(nd, xv, n, inv, smax, t0, t1, tx)) continue;
       if (!(nd.meta & kMetaLeaf) && cell_opens(a, q, nd, x, si)) {
-        const bool lower_first = in_lower_half(nd, xv);
-        lstk[sp] = lower_first ? nd.child + 1 : nd.child;
-        lstk[sp + 1] = lower_first ? nd.child : nd.child + 1;
-        sp += 2;
+        bool lower_first, lower_hit, upper_hit;
+        crossed_halves(nd, xv, n, inv, t0, t1, lower_first, lower_hit, upper_hit);
+        const bool near_hit = lower_first ? lower_hit : upper_hit;
+        const bool far_hit = lower_first ? upper_hit : lower_hit;
+        if (far_hit) lstk[sp++] = lower_first ? nd.child + 1 : nd.child;
+        if (near_hit) lstk[sp++] = lower_first ? nd.child : nd.child + 1;
         continue;
       }
       const BandVec<NBP> al =
@@ -325,10 +327,12 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
         if (!beam_chord(nd, xv, n, inv, smax, t0, t1, tx)) continue;
         if (!(nd.meta & kMetaLeaf) && cell_opens(a, q, nd, x, si)) {
           // far half on top of the stack
-          const bool lower_first = in_lower_half(nd, xv);
-          lstk[sp] = lower_first ? nd.child : nd.child + 1;
-          lstk[sp + 1] = lower_first ? nd.child + 1 : nd.child;
-          sp += 2;
+          bool lower_first, lower_hit, upper_hit;
+          crossed_halves(nd, xv, n, inv, t0, t1, lower_first, lower_hit, upper_hit);
+          const bool near_hit = lower_first ? lower_hit : upper_hit;
+          const bool far_hit = lower_first ? upper_hit : lower_hit;
+          if (near_hit) lstk[sp++] = lower_first ? nd.child : nd.child + 1;
+          if (far_hit) lstk[sp++] = lower_first ? nd.child + 1 : nd.child;
           continue;
         }
         float* d = (nd.meta & kMetaLeaf) ? g.g_aleaf + int64_t(q) * NBP

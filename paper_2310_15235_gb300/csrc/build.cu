@@ -472,6 +472,10 @@ __global__ void k_aggregate_level(int64_t lb, int64_t le, int nb, int nbp, doubl
   w.aux = c < 0 ? first[q] : int_index[q];
   w.count = count[q];
   w.meta = uint32_t(d) | (uint32_t(d % 3) << kMetaAxisShift) | (c < 0 ? kMetaLeaf : 0u) | has;
+  if (c >= 0) {
+    if (flags64[c] & kMetaHasAlpha) w.meta |= kMetaChild0Alpha;
+    if (flags64[c + 1] & kMetaHasAlpha) w.meta |= kMetaChild1Alpha;
+  }
   nodes[q] = w;
 }
 

@@ -33,6 +33,8 @@ constexpr uint32_t kMetaLeaf = 1u << 8;
 constexpr uint32_t kMetaHasL = 1u << 9;      // some luminosity below
 constexpr uint32_t kMetaHasAlpha = 1u << 10; // some absorption below
 constexpr int kMetaAxisShift = 12;            // split axis (depth mod 3) in bits 12-13
+constexpr uint32_t kMetaChild0Alpha = 1u << 14;  // lower half has some absorption
+constexpr uint32_t kMetaChild1Alpha = 1u << 15;  // upper half has some absorption
 
 // Source found by the cut, binned to its beam: projected distance s along
 // the beam, r/s, the geometric kernel g(r), and where its luminosity lives.

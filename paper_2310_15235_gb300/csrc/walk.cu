@@ -39,8 +39,7 @@ namespace trevr2 {
 // Phase A: lanes take beams (those with sources) from a per-warp counter.
 template <int NBP>
 __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int* lstk,
-                             const SrcEntry* V, const int* off, int* next_beam, float* Js,
-                             float* Jc) {
+                             const SrcEntry* V, float* T, const int* off, int* next_beam) {
   int k = lane;
   for (;;) {
     while (k < a.npix && (k ? off[k - 1] : 0) == off[k]) k = atomicAdd(next_beam, 1);
@@ -81,53 +80,59 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
       }
       if (!hit || !(t0 < t1)) continue;
       if (!(nd.meta & kMetaLeaf) && cell_opens(a, q, nd, x, si)) {
-        // near half (the side of the receiver) on top of the stack
-        const bool lower_first = in_lower_half(nd, xv);
-        lstk[sp] = lower_first ? nd.child + 1 : nd.child;
-        lstk[sp + 1] = lower_first ? nd.child : nd.child + 1;
-        sp += 2;
+        // the crossed halves, the near one (the side of the receiver) on top
+        bool lower_first, lower_hit, upper_hit;
+        crossed_halves(nd, xv, n, inv, t0, t1, lower_first, lower_hit, upper_hit);
+        const bool near_hit = lower_first ? lower_hit : upper_hit;
+        const bool far_hit = lower_first ? upper_hit : lower_hit;
+        if (far_hit) lstk[sp++] = lower_first ? nd.child + 1 : nd.child;
+        if (near_hit) lstk[sp++] = lower_first ? nd.child : nd.child + 1;
         continue;
       }
       const BandVec<NBP> al = (nd.meta & kMetaLeaf)
                                   ? load_bands<NBP>(a.alpha_leaf + int64_t(q) * NBP)
                                   : load_bands<NBP>(a.alpha_tab + (int64_t(nd.aux) * a.P + pair) * NBP);
       while (ptr < end) {
-        const SrcEntry src = V[ptr];
-        if (!(src.s < t1)) break;
-        const float ds = fmaxf(0.0f, src.s - t0);
-        const float* Lp = (src.ref & kRefElement) ? a.Lelem + int64_t(src.ref & 0x7fffffff) * NBP
-                                                  : a.Lnode + int64_t(src.ref) * NBP;
-        const BandVec<NBP> L = load_bands<NBP>(Lp);
+        const float s_ = V[ptr].s;
+        if (!(s_ < t1)) break;
+        const float ds = fmaxf(0.0f, s_ - t0);
+        BandVec<NBP> tk;
 #pragma unroll
-        for (int b = 0; b < NBP; ++b) {
-          const float term = L.v[b] * src.w * expf(-(tau[b] + al.v[b] * ds) * src.rs);
-          const float y = term - Jc[b];
-          const float t = Js[b] + y;
-          Jc[b] = (t - Js[b]) - y;
-          Js[b] = t;
-        }
+        for (int b = 0; b < NBP; ++b) tk.v[b] = tau[b] + al.v[b] * ds;
+        store_bands<NBP>(T + int64_t(ptr) * NBP, tk);
         ++ptr;
       }
 #pragma unroll
       for (int b = 0; b < NBP; ++b) tau[b] += al.v[b] * (t1 - t0);
     }
     // sources beyond the last absorbing cell of the beam
-    while (ptr < end) {
-      const SrcEntry src = V[ptr];
-      const float* Lp = (src.ref & kRefElement) ? a.Lelem + int64_t(src.ref & 0x7fffffff) * NBP
-                                                : a.Lnode + int64_t(src.ref) * NBP;
-      const BandVec<NBP> L = load_bands<NBP>(Lp);
+    BandVec<NBP> tk;
 #pragma unroll
-      for (int b = 0; b < NBP; ++b) {
-        const float term = L.v[b] * src.w * expf(-tau[b] * src.rs);
-        const float y = term - Jc[b];
-        const float t = Js[b] + y;
-        Jc[b] = (t - Js[b]) - y;
-        Js[b] = t;
-      }
-      ++ptr;
-    }
+    for (int b = 0; b < NBP; ++b) tk.v[b] = tau[b];
+    for (; ptr < end; ++ptr) store_bands<NBP>(T + int64_t(ptr) * NBP, tk);
     k = atomicAdd(next_beam, 1);
+  }
+}
+
+// The n staged sources, all lanes at once: J_b += L_b g(r) e^{-tau_k(s) r/s}
+// with a compensated FP32 sum per lane.
+template <int NBP>
+__device__ __forceinline__ void eval_sources(const WalkArgs& a, int lane, const SrcEntry* V,
+                                             const float* T, int n, float* Js, float* Jc) {
+  for (int e = lane; e < n; e += 32) {
+    const SrcEntry src = V[e];
+    const float* Lp = (src.ref & kRefElement) ? a.Lelem + int64_t(src.ref & 0x7fffffff) * NBP
+                                              : a.Lnode + int64_t(src.ref) * NBP;
+    const BandVec<NBP> L = load_bands<NBP>(Lp);
+    const BandVec<NBP> tk = load_bands<NBP>(T + int64_t(e) * NBP);
+#pragma unroll
+    for (int b = 0; b < NBP; ++b) {
+      const float term = L.v[b] * src.w * expf(-tk.v[b] * src.rs);
+      const float y = term - Jc[b];
+      const float t = Js[b] + y;
+      Jc[b] = (t - Js[b]) - y;
+      Js[b] = t;
+    }
   }
 }
 
@@ -136,7 +141,7 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
 template <int NBP>
 __device__ __forceinline__ void walk_receiver(const WalkArgs& a, int64_t io, float* Jrow, int lane,
                                               int* stk, int* off, int* next_beam, int* lstk,
-                                              SrcEntry* U, int* Up, SrcEntry* V) {
+                                              SrcEntry* U, int* Up, SrcEntry* V, float* T) {
   if (io < 0 || io >= a.N) {
     if (lane == 0) atomicOr(a.status, kStatusBadActive);
     if (lane < a.nbsel) Jrow[lane] = __int_as_float(0x7fc00000);
@@ -156,7 +161,9 @@ __device__ __forceinline__ void walk_receiver(const WalkArgs& a, int64_t io, flo
       bin_sources(a, lane, U, Up, n, V, off);
       if (lane == 0) *next_beam = 32;
       __syncwarp();
-      phase_absorb<NBP>(a, x, si, lane, lstk, V, off, next_beam, Js, Jc);
+      phase_absorb<NBP>(a, x, si, lane, lstk, V, T, off, next_beam);
+      __syncwarp();
+      eval_sources<NBP>(a, lane, V, T, n, Js, Jc);
       __syncwarp();
     }
     if (lo + a.M >= total) break;
@@ -201,13 +208,14 @@ __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk(Wa
   SrcEntry* U = a.srcU + gw * a.M;
   int* Up = a.pixU + gw * a.M;
   SrcEntry* V = a.srcV + gw * a.M;
+  float* T = a.srcT + gw * a.M * 4;
   for (;;) {
     unsigned long long slot = 0;
     if (lane == 0) slot = atomicAdd(a.counter, 1ull);
     slot = __shfl_sync(0xffffffffu, slot, 0);
     if (slot >= (unsigned long long)a.A) break;
     walk_receiver<NBP>(a, a.active[slot], a.J + int64_t(slot) * a.nbsel, lane, stk, off, next_beam,
-                       lstk, U, Up, V);
+                       lstk, U, Up, V, T);
   }
 }
 
@@ -229,6 +237,7 @@ struct BatchArgs {
   SrcEntry* srcU;
   int* pixU;
   SrcEntry* srcV;
+  float* srcT;
   int M;
   int stack_ints;
   int npix;
@@ -249,6 +258,7 @@ __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk_ba
   SrcEntry* U = B.srcU + gw * B.M;
   int* Up = B.pixU + gw * B.M;
   SrcEntry* V = B.srcV + gw * B.M;
+  float* T = B.srcT + gw * B.M * 4;
   for (;;) {
     unsigned long long r = 0;
     int t = 0;
@@ -267,7 +277,7 @@ __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk_ba
     t = __shfl_sync(0xffffffffu, t, 0);
     if (r >= (unsigned long long)B.total) break;
     walk_receiver<NBP>(B.tree[t], B.active[r], B.J + int64_t(r) * B.nbsel, lane, stk, off,
-                       next_beam, lstk, U, Up, V);
+                       next_beam, lstk, U, Up, V, T);
   }
 }
 
@@ -352,14 +362,15 @@ int config_walk_kernel(const void* fn, int warps, size_t smem, int* per_sm, int*
 
 // Walk buffers: per warp, M source records in and out and their beams.
 static size_t walk_buffer_bytes(size_t warps, int M) {
-  return warps * size_t(M) * (2 * sizeof(SrcEntry) + sizeof(int));
+  return warps * size_t(M) * (2 * sizeof(SrcEntry) + 4 * sizeof(float) + sizeof(int));
 }
 
 static void place_walk_buffers(char* base, size_t warps, int M, SrcEntry** U, SrcEntry** V,
-                               int** Up) {
+                               float** T, int** Up) {
   *U = reinterpret_cast<SrcEntry*>(base);
   *V = reinterpret_cast<SrcEntry*>(base + warps * M * sizeof(SrcEntry));
-  *Up = reinterpret_cast<int*>(base + 2 * warps * M * sizeof(SrcEntry));
+  *T = reinterpret_cast<float*>(base + 2 * warps * M * sizeof(SrcEntry));
+  *Up = reinterpret_cast<int*>(base + 2 * warps * M * sizeof(SrcEntry) + warps * M * 4 * sizeof(float));
 }
 
 static int launch_walk(Tree* t, Table* tb, const int64_t* active, int64_t A, int nside,
@@ -387,7 +398,7 @@ static int launch_walk(Tree* t, Table* tb, const int64_t* active, int64_t A, int
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(walk buffers)");
     t->scratch_bytes = need;
   }
-  place_walk_buffers(static_cast<char*>(t->scratch), warps, a.M, &a.srcU, &a.srcV, &a.pixU);
+  place_walk_buffers(static_cast<char*>(t->scratch), warps, a.M, &a.srcU, &a.srcV, &a.srcT, &a.pixU);
   T2_CUDA(cudaMemsetAsync(t->counter, 0, sizeof(unsigned long long), st));
   void* args[] = {&a};
   T2_CUDA(cudaLaunchKernel(fn, dim3(unsigned(blocks)), dim3(kWalkWarps * 32), args, smem, st));
@@ -513,7 +524,7 @@ static int batch_shape(Batch* b, int warps, int M, int64_t limit, const void** f
     b->scratch_bytes = need;
   }
   place_walk_buffers(static_cast<char*>(b->scratch), nw, M, &b->args.srcU, &b->args.srcV,
-                     &b->args.pixU);
+                     &b->args.srcT, &b->args.pixU);
   b->args.M = M;
   for (size_t i = 0; i < b->trees.size(); ++i) b->args.tree[i].M = M;
   return TREVR2_OK;
@@ -871,7 +882,7 @@ static int launch_walk_noalloc(Tree* t, Table* tb, const int64_t* active, int64_
   blocks = std::min<int64_t>(blocks, max_blocks);
   blocks = std::max<int64_t>(blocks, 1);
   const size_t warps = size_t(blocks) * kWalkWarps;
-  place_walk_buffers(static_cast<char*>(scratch), warps, a.M, &a.srcU, &a.srcV, &a.pixU);
+  place_walk_buffers(static_cast<char*>(scratch), warps, a.M, &a.srcU, &a.srcV, &a.srcT, &a.pixU);
   T2_CUDA(cudaMemsetAsync(t->counter, 0, sizeof(unsigned long long), st));
   void* args[] = {&a};
   T2_CUDA(cudaLaunchKernel(fn, dim3(unsigned(blocks)), dim3(kWalkWarps * 32), args, smem, st));

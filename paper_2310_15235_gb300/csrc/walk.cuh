@@ -51,6 +51,7 @@ struct WalkArgs {
   SrcEntry* srcU;
   int* pixU;
   SrcEntry* srcV;
+  float* srcT;      // [warps][M][4] optical depth tau_k(s) of every staged source
   int M;
   int stack_ints;   // per warp
   int max_depth;
@@ -65,15 +66,35 @@ __device__ __forceinline__ float3 node_ext(uint32_t meta) {
                      __int_as_float((127 - splits_on_axis(d, 2)) << 23));
 }
 
-// Whether x lies in the lower half of node nd along the node's split axis
-// (selects instead of an index, which would put the operands in local memory).
-__device__ __forceinline__ bool in_lower_half(const NodeW& nd, const float xv[3]) {
+// The halves of an opened node that a beam (x + t n, t in [t0, t1), the
+// node's own chord) crosses and that hold some absorption, and which half
+// the beam meets first (the receiver's side).  The crossing time of the
+// split plane is the face time each half computes for itself, so a half is
+// reported crossed exactly when its own chord test would find t0 < t1.
+__device__ __forceinline__ void crossed_halves(const NodeW& nd, const float xv[3], const float n[3],
+                                               const float inv[3], float t0, float t1,
+                                               bool& lower_first, bool& lower_hit,
+                                               bool& upper_hit) {
   const int axis = int(nd.meta & kMetaDepthMask) % 3;
   const float3 e = node_ext(nd.meta);
   const float lo = axis == 0 ? nd.lo[0] : (axis == 1 ? nd.lo[1] : nd.lo[2]);
   const float ex = axis == 0 ? e.x : (axis == 1 ? e.y : e.z);
   const float xa = axis == 0 ? xv[0] : (axis == 1 ? xv[1] : xv[2]);
-  return xa < lo + 0.5f * ex;
+  const float na = axis == 0 ? n[0] : (axis == 1 ? n[1] : n[2]);
+  const float ia = axis == 0 ? inv[0] : (axis == 1 ? inv[1] : inv[2]);
+  const float mid = lo + 0.5f * ex;
+  lower_first = xa < mid;
+  if (na == 0.0f) {
+    lower_hit = lower_first;
+    upper_hit = !lower_first;
+  } else {
+    const float tm = (mid - xa) * ia;
+    const bool first = t0 < fminf(t1, tm), second = fmaxf(t0, tm) < t1;
+    lower_hit = na > 0.0f ? first : second;
+    upper_hit = na > 0.0f ? second : first;
+  }
+  lower_hit &= (nd.meta & kMetaChild0Alpha) != 0;
+  upper_hit &= (nd.meta & kMetaChild1Alpha) != 0;
 }
 
 // FP64 opening decision, the definition evaluated without contraction.
@@ -333,6 +354,17 @@ __device__ __forceinline__ BandVec<NBP> load_bands(const float* p) {
     r.v[0] = *p;
   }
   return r;
+}
+
+template <int NBP>
+__device__ __forceinline__ void store_bands(float* p, const BandVec<NBP>& v) {
+  if constexpr (NBP == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v.v[0], v.v[1], v.v[2], v.v[3]);
+  } else if constexpr (NBP == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(v.v[0], v.v[1]);
+  } else {
+    *p = v.v[0];
+  }
 }
 
 // ---------------------------------------------------------------------------
