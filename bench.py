@@ -328,6 +328,7 @@ def run_ours(args, world, rank, local):
     if world == 1 and not args.no_adjoint:
         line["adjoint"] = run_adjoint(args, dev)
         line["adjoint_forward_ratio"] = line["adjoint"]["ratio"]
+        line["adjoint"]["clumpy_2M"] = run_adjoint_clumpy(case, inp, dev)
     if world == 1 and not args.no_batched:
         per_rec = roofline["algorithmic_bytes_per_unit"] * npix * nb if roofline else None
         line["batched"] = run_batched(args, dev, per_rec, hbm_peak, peak_kind)
@@ -478,6 +479,41 @@ def run_adjoint(args, dev):
             "backward_units_per_s": units / (bwd * 1e-3)}
 
 
+def run_adjoint_clumpy(case, inp, dev):
+    """Adjoint / forward on the benchmark field itself (2,097,152 receivers,
+    nside 4, 3 bands), Loss = sum w J with w ~ U(0,1); one warm-up and two
+    timed calls of each."""
+    import torch
+
+    import paper_2310_15235_gb300 as t2
+
+    tree = t2.build(inp["pos"], inp["mass"], inp["kappa"], inp["lum"], inp["h"], case["box_lo"],
+                    case["box_size"], case["bucket"], device=dev)
+    tree.prepare(case["nside"])
+    A, nb = len(case["active"]), case["nb"]
+    w = torch.rand((A, nb), device=dev, generator=torch.Generator(dev).manual_seed(6))
+    J = torch.empty((A, nb), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tree.status()
+        return e0.elapsed_time(e1) / reps
+
+    fwd = timed(lambda: tree.J(inp["active"], case["nside"], case["theta"], out=J, flags=t2.ASYNC))
+    bwd = timed(lambda: tree.J_backward(inp["active"], w, case["nside"], case["theta"],
+                                        flags=t2.ASYNC))
+    tree.free()
+    return {"forward_ms": fwd, "backward_ms": bwd, "ratio": bwd / fwd}
+
+
 def run_walk_only(args):
     """The walk kernel alone on a clumpy field of lattice^3 gas (profiling
     aid): tree and tables built once, then `warmup + steps` walks."""
@@ -530,9 +566,17 @@ def main():
     ap.add_argument("--batched-reps", type=int, default=2)
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the adjoint / forward timing")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="time only the forward and adjoint walks on the 64^3 adjoint field "
+                         "(profiling)")
     args = ap.parse_args()
     if args.walk_only:
         run_walk_only(args)
+        return
+    if args.adjoint_only:
+        import torch
+        print(json.dumps({"mode": "adjoint-only",
+                          **run_adjoint(args, torch.device("cuda", 0))}), flush=True)
         return
     world, rank, local = _dist_setup()
     if args.impl == "reference":
