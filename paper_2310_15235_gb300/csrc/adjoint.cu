@@ -50,17 +50,32 @@ struct AdjArgs {
   float* g_atab;     // [n_internal][P][NBP] dLoss/dalpha of accepted internal cells
   float* g_aleaf;    // [n][NBP] dLoss/dalpha_leaf
   float* g_Lnode;    // [n][NBP] dLoss/dL of cells as point sources
-  float* g_c;        // [n][3] dLoss/d(centre of luminosity), normalised units
+  float4* g_c;       // [n] dLoss/d(centre of luminosity), normalised units (w unused)
   float* g_Lelem;    // [N][NBP] dLoss/dL of elements as point sources (sorted order)
   float* g_thick;    // [N][NBP] Eq. taucorr's dLoss/dkappa (sorted order)
-  float* Q;          // [warps][M][NBP] q_b = c_b r/s per staged source
+  float* T;          // [warps][M][NBP] tau_k(s) of every staged source
+  float* Q;          // [warps][M][NBP] alpha at s, then q_b = c_b r/s
   float4* seg;       // [warps][seg_cap][32] per lane: segment target, t0, t1
-  int seg_cap;       // segments recorded per lane and beam (0: always re-walk)
+  int seg_cap;       // segments recorded per lane and pass (0: always walk again)
 };
 
-// Segments of one beam recorded front to back, replayed back to front.
-constexpr int kSegCap = 64;
+// Segments recorded front to back, replayed back to front: per lane and pass.
+constexpr int kSegCap = 128;
 constexpr int kAdjWarps = 8;  // warps per block of the adjoint walk
+// Beam record in shared memory: recording lane (5 bits), first record
+// (13 bits), count (14 bits); kBeamRewalk marks a beam whose records did not fit.
+constexpr uint32_t kBeamRewalk = 0x3fffu;
+
+template <int NBP>
+__device__ __forceinline__ void add_bands(float* __restrict__ dst, const float* v) {
+  if constexpr (NBP == 4) {
+    atomicAdd(reinterpret_cast<float4*>(dst), make_float4(v[0], v[1], v[2], v[3]));
+  } else if constexpr (NBP == 2) {
+    atomicAdd(reinterpret_cast<float2*>(dst), make_float2(v[0], v[1]));
+  } else {
+    atomicAdd(dst, v[0]);
+  }
+}
 
 // The absorption gradient of one segment [t0, t1) of a beam (back to front):
 // W holds sum q over the sources beyond t1, p2 the nearest source not yet
@@ -88,12 +103,15 @@ __device__ __forceinline__ void segment_gradient(float* __restrict__ dst, float 
     }
     --p2;
   }
+  float ga[NBP];
+  bool any = false;
 #pragma unroll
   for (int b = 0; b < NBP; ++b) {
-    const float ga = -(W[b] * (t1 - t0) + gin[b]);
-    if (ga != 0.0f) atomicAdd(dst + b, ga);
+    ga[b] = -(W[b] * (t1 - t0) + gin[b]);
+    any |= ga[b] != 0.0f;
     W[b] += win[b];
   }
+  if (any) add_bands<NBP>(dst, ga);
 }
 
 // d ln g / dr of Eq. intint's kernel g(r) = G(x)/h^2, x = r/(0.4886 h).
@@ -172,64 +190,19 @@ __device__ __forceinline__ bool beam_chord(const NodeW& nd, const float xv[3], c
   return hit && (t0 < t1);
 }
 
-// One source seen front to back: its term of J, dLoss/dL, dLoss/dc and q.
-// tau_k(s) = tau + al ds; as_ is the absorption at s (dtau_k/ds).
+// Stage 1, lanes take beams with sources: each walks its beam front to back
+// (near half first), records tau_k(s) and the absorption at s of every
+// source and the beam's absorbing segments.
 template <int NBP>
-__device__ __forceinline__ void source_adjoint(const AdjArgs& g, const SrcEntry& src, float3 x,
-                                               const float n[3], const float* tau,
-                                               const BandVec<NBP>& al, float ds,
-                                               const BandVec<NBP>& as_, float* Qrow,
-                                               const float* gJf, float* Js, float* Jc, float hr) {
+__device__ void adjoint_stage1(const AdjArgs& g, float3 x, int si, int lane, int* lstk,
+                               const SrcEntry* V, float* T, float* Q, float4* S, const int* off,
+                               uint32_t* binfo, int* next_beam) {
   const WalkArgs& a = g.w;
-  const bool elem = (src.ref & kRefElement) != 0;
-  const int64_t idx = src.ref & 0x7fffffff;
-  const BandVec<NBP> L = load_bands<NBP>(elem ? a.Lelem + idx * NBP : a.Lnode + idx * NBP);
-  float* gL = elem ? g.g_Lelem + idx * NBP : g.g_Lnode + idx * NBP;
-  float cb[NBP], tk[NBP];
-#pragma unroll
-  for (int b = 0; b < NBP; ++b) {
-    tk[b] = tau[b] + al.v[b] * ds;
-    const float e = expf(-tk[b] * src.rs);
-    const float term = L.v[b] * src.w * e;
-    const float y = term - Jc[b];
-    const float t = Js[b] + y;
-    Jc[b] = (t - Js[b]) - y;
-    Js[b] = t;
-    const float dL = gJf[b] * src.w * e;
-    if (dL != 0.0f) atomicAdd(gL + b, dL);
-    cb[b] = dL * L.v[b];
-    Qrow[b] = cb[b] * src.rs;
-  }
-  if (!elem) {
-    const float4 c = a.csrc[idx];
-    const float vx = c.x - x.x, vy = c.y - x.y, vz = c.z - x.z;
-    const float r = sqrtf(vx * vx + vy * vy + vz * vz);
-    const float ir = 1.0f / r;
-    const float dlg = (a.flags & TREVR2_SOFT) ? soft_dlog(r, hr) : -2.0f * ir;
-    float fr = 0.0f, fn = 0.0f;  // coefficients of rhat and n
-#pragma unroll
-    for (int b = 0; b < NBP; ++b) {
-      fr += cb[b] * (dlg - tk[b] / src.s);
-      fn += cb[b] * src.rs * (tk[b] / src.s - as_.v[b]);
-    }
-    if (fr != 0.0f || fn != 0.0f) {
-      float* gc = g.g_c + 3 * idx;
-      atomicAdd(gc + 0, fr * vx * ir + fn * n[0]);
-      atomicAdd(gc + 1, fr * vy * ir + fn * n[1]);
-      atomicAdd(gc + 2, fr * vz * ir + fn * n[2]);
-    }
-  }
-}
-
-// Lanes take beams with sources; each walks its beam front to back and then
-// back to front (see the file comment).
-template <int NBP>
-__device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int* lstk,
-                               const SrcEntry* V, float* Q, float4* S, const int* off,
-                               int* next_beam, const float* gJf, float* Js, float* Jc) {
-  const WalkArgs& a = g.w;
-  const float hr = a.hn[si];
   const float xv[3] = {x.x, x.y, x.z};
+  BandVec<NBP> zero;
+#pragma unroll
+  for (int b = 0; b < NBP; ++b) zero.v[b] = 0.0f;
+  int nrec = 0;
   int k = lane;
   for (;;) {
     while (k < a.npix && (k ? off[k - 1] : 0) == off[k]) k = atomicAdd(next_beam, 1);
@@ -243,11 +216,6 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
     float inv[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) inv[c] = n[c] != 0.0f ? 1.0f / n[c] : 0.0f;
-
-    // front to back: tau at every source
-    BandVec<NBP> zero;
-#pragma unroll
-    for (int b = 0; b < NBP; ++b) zero.v[b] = 0.0f;
     float tau[NBP];
 #pragma unroll
     for (int b = 0; b < NBP; ++b) tau[b] = 0.0f;
@@ -255,8 +223,9 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
     // farthest sources lie in it when it was clipped at smax)
     float seg_t0 = 0.0f, seg_x = 0.0f;
     BandVec<NBP> seg_al = zero;
-    int nseg = 0;
+    const int first = nrec;
     int ptr = start;
+    float s_next = V[ptr].s;
     int sp = 1;
     lstk[0] = 0;
     while (sp > 0 && ptr < end) {
@@ -267,7 +236,9 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
       if (!beam_chord(nd, xv, n, inv, smax, t0, t1, tx)) continue;
       if (!(nd.meta & kMetaLeaf) && cell_opens(a, q, nd, x, si)) {
         bool lower_first, lower_hit, upper_hit;
-        crossed_halves(nd, xv, n, inv, t0, t1, lower_first, lower_hit, upper_hit);
+        float lt0, lt1, ut0, ut1;
+        crossed_halves(nd, xv, n, inv, t0, t1, lower_first, lower_hit, upper_hit, lt0, lt1, ut0,
+                       ut1);
         const bool near_hit = lower_first ? lower_hit : upper_hit;
         const bool far_hit = lower_first ? upper_hit : lower_hit;
         if (far_hit) lstk[sp++] = lower_first ? nd.child + 1 : nd.child;
@@ -277,17 +248,20 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
       const BandVec<NBP> al =
           (nd.meta & kMetaLeaf) ? load_bands<NBP>(a.alpha_leaf + int64_t(q) * NBP)
                                 : load_bands<NBP>(a.alpha_tab + (int64_t(nd.aux) * a.P + pair) * NBP);
-      if (nseg < g.seg_cap) {
+      if (nrec < g.seg_cap) {
         const int dst = (nd.meta & kMetaLeaf) ? -(q + 1) : nd.aux * a.P + pair;
-        S[nseg * 32 + lane] = make_float4(__int_as_float(dst), t0, t1, 0.0f);
+        S[nrec * 32 + lane] = make_float4(__int_as_float(dst), t0, t1, 0.0f);
       }
-      ++nseg;
-      while (ptr < end) {
-        const SrcEntry src = V[ptr];
-        if (!(src.s < t1)) break;
-        source_adjoint<NBP>(g, src, x, n, tau, al, fmaxf(0.0f, src.s - t0),
-                            src.s > t0 ? al : zero, Q + int64_t(ptr) * NBP, gJf, Js, Jc, hr);
+      ++nrec;
+      while (s_next < t1) {
+        const float ds = fmaxf(0.0f, s_next - t0);
+        BandVec<NBP> tk;
+#pragma unroll
+        for (int b = 0; b < NBP; ++b) tk.v[b] = tau[b] + al.v[b] * ds;
+        store_bands<NBP>(T + int64_t(ptr) * NBP, tk);
+        store_bands<NBP>(Q + int64_t(ptr) * NBP, s_next > t0 ? al : zero);
         ++ptr;
+        s_next = ptr < end ? V[ptr].s : INFINITY;
       }
 #pragma unroll
       for (int b = 0; b < NBP; ++b) tau[b] += al.v[b] * (t1 - t0);
@@ -295,29 +269,113 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
       seg_x = tx;
       seg_al = al;
     }
+    BandVec<NBP> tk;
+#pragma unroll
+    for (int b = 0; b < NBP; ++b) tk.v[b] = tau[b];
     for (; ptr < end; ++ptr) {
-      const SrcEntry src = V[ptr];
-      const bool in_seg = src.s > seg_t0 && src.s < seg_x;
-      source_adjoint<NBP>(g, src, x, n, tau, zero, 0.0f, in_seg ? seg_al : zero,
-                          Q + int64_t(ptr) * NBP, gJf, Js, Jc, hr);
+      const float s_ = V[ptr].s;
+      store_bands<NBP>(T + int64_t(ptr) * NBP, tk);
+      store_bands<NBP>(Q + int64_t(ptr) * NBP, s_ > seg_t0 && s_ < seg_x ? seg_al : zero);
     }
+    const uint32_t count = nrec <= g.seg_cap ? uint32_t(nrec - first) : kBeamRewalk;
+    binfo[k] = uint32_t(lane) | ((uint32_t(first) & 0x1fffu) << 5) | (count << 18);
+    k = atomicAdd(next_beam, 1);
+  }
+}
 
-    // back to front: the absorption gradient of every segment, from the
-    // recorded segments or, when a beam had more, by walking it again with
-    // the far half first
+// Stage 2, all lanes over the staged sources: the term of J, dLoss/dL,
+// dLoss/dc (cells only) and q_b = c_b r/s, with c_b = gJ_b F_b L_b w e^{-tau_b}
+// and dtau/dc = (r/s) alpha(s) n + (tau_k(s)/s) (rhat - (r/s) n).
+template <int NBP>
+__device__ void adjoint_stage2(const AdjArgs& g, float3 x, int si, int lane, const SrcEntry* V,
+                               const int* Up, const float* T, float* Q, int n, const float* gJf,
+                               float* Js, float* Jc) {
+  const WalkArgs& a = g.w;
+  const float hr = a.hn[si];
+  const bool soft = (a.flags & TREVR2_SOFT) != 0;
+  for (int e = lane; e < n; e += 32) {
+    const SrcEntry src = V[e];
+    const bool elem = (src.ref & kRefElement) != 0;
+    const int64_t idx = src.ref & 0x7fffffff;
+    const BandVec<NBP> L = load_bands<NBP>(elem ? a.Lelem + idx * NBP : a.Lnode + idx * NBP);
+    const BandVec<NBP> tk = load_bands<NBP>(T + int64_t(e) * NBP);
+    const BandVec<NBP> as = load_bands<NBP>(Q + int64_t(e) * NBP);
+    float dL[NBP], cb[NBP];
+    BandVec<NBP> qv;
+    bool any = false;
+#pragma unroll
+    for (int b = 0; b < NBP; ++b) {
+      const float ex = expf(-tk.v[b] * src.rs);
+      const float term = L.v[b] * src.w * ex;
+      const float y = term - Jc[b];
+      const float t = Js[b] + y;
+      Jc[b] = (t - Js[b]) - y;
+      Js[b] = t;
+      dL[b] = gJf[b] * src.w * ex;
+      any |= dL[b] != 0.0f;
+      cb[b] = dL[b] * L.v[b];
+      qv.v[b] = cb[b] * src.rs;
+    }
+    store_bands<NBP>(Q + int64_t(e) * NBP, qv);
+    if (any) add_bands<NBP>(elem ? g.g_Lelem + idx * NBP : g.g_Lnode + idx * NBP, dL);
+    if (!elem) {
+      const float4 c = a.csrc[idx];
+      const float vx = c.x - x.x, vy = c.y - x.y, vz = c.z - x.z;
+      const float r = sqrtf(vx * vx + vy * vy + vz * vz);
+      const float ir = 1.0f / r;
+      const float dlg = soft ? soft_dlog(r, hr) : -2.0f * ir;
+      const float4 nk = a.dirs[Up[e]];
+      float fr = 0.0f, fn = 0.0f;  // coefficients of rhat and n
+#pragma unroll
+      for (int b = 0; b < NBP; ++b) {
+        fr += cb[b] * (dlg - tk.v[b] / src.s);
+        fn += cb[b] * src.rs * (tk.v[b] / src.s - as.v[b]);
+      }
+      if (fr != 0.0f || fn != 0.0f)
+        atomicAdd(g.g_c + idx, make_float4(fr * vx * ir + fn * nk.x, fr * vy * ir + fn * nk.y,
+                                           fr * vz * ir + fn * nk.z, 0.0f));
+    }
+  }
+}
+
+// Stage 3, lanes take beams again: the absorption gradient of every segment,
+// back to front, from the records (or walking the beam again, far half
+// first, when they did not fit).
+template <int NBP>
+__device__ void adjoint_stage3(const AdjArgs& g, float3 x, int si, int lane, int* lstk,
+                               const SrcEntry* V, const float* Q, const float4* S, const int* off,
+                               const uint32_t* binfo, int* next_beam) {
+  const WalkArgs& a = g.w;
+  const float xv[3] = {x.x, x.y, x.z};
+  int k = lane;
+  for (;;) {
+    while (k < a.npix && (k ? off[k - 1] : 0) == off[k]) k = atomicAdd(next_beam, 1);
+    if (k >= a.npix) break;
+    const int start = k ? off[k - 1] : 0;
+    const int end = off[k];
+    const uint32_t info = binfo[k];
+    const uint32_t count = info >> 18;
     float W[NBP];
 #pragma unroll
     for (int b = 0; b < NBP; ++b) W[b] = 0.0f;
     int p2 = end - 1;
-    if (nseg <= g.seg_cap) {
-      for (int j = nseg - 1; j >= 0; --j) {
-        const float4 r = S[j * 32 + lane];
+    if (count != kBeamRewalk) {
+      const int rl = int(info & 31u), first = int((info >> 5) & 0x1fffu);
+      for (int j = int(count) - 1; j >= 0; --j) {
+        const float4 r = S[(first + j) * 32 + rl];
         const int dst = __float_as_int(r.x);
         float* d = dst < 0 ? g.g_aleaf + int64_t(-dst - 1) * NBP : g.g_atab + int64_t(dst) * NBP;
         segment_gradient<NBP>(d, r.y, r.z, V, Q, start, p2, W);
       }
     } else {
-      sp = 1;
+      const float smax = V[end - 1].s;
+      const float4 dn = a.dirs[k];
+      const int pair = __float_as_int(dn.w);
+      const float n[3] = {dn.x, dn.y, dn.z};
+      float inv[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) inv[c] = n[c] != 0.0f ? 1.0f / n[c] : 0.0f;
+      int sp = 1;
       lstk[0] = 0;
       while (sp > 0) {
         const int q = lstk[--sp];
@@ -328,7 +386,9 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
         if (!(nd.meta & kMetaLeaf) && cell_opens(a, q, nd, x, si)) {
           // far half on top of the stack
           bool lower_first, lower_hit, upper_hit;
-          crossed_halves(nd, xv, n, inv, t0, t1, lower_first, lower_hit, upper_hit);
+          float lt0, lt1, ut0, ut1;
+          crossed_halves(nd, xv, n, inv, t0, t1, lower_first, lower_hit, upper_hit, lt0, lt1,
+                         ut0, ut1);
           const bool near_hit = lower_first ? lower_hit : upper_hit;
           const bool far_hit = lower_first ? upper_hit : lower_hit;
           if (near_hit) lstk[sp++] = lower_first ? nd.child : nd.child + 1;
@@ -346,8 +406,9 @@ __device__ void absorb_adjoint(const AdjArgs& g, float3 x, int si, int lane, int
 
 template <int NBP>
 __device__ __forceinline__ void adjoint_receiver(const AdjArgs& g, int64_t slot, int lane, int* stk,
-                                                 int* off, int* next_beam, int* lstk, SrcEntry* U,
-                                                 int* Up, SrcEntry* V, float* Q, float4* S) {
+                                                 int* off, uint32_t* binfo, int* next_beam,
+                                                 int* lstk, SrcEntry* U, int* Up, SrcEntry* V,
+                                                 float* T, float* Q, float4* S) {
   const WalkArgs& a = g.w;
   const int64_t io = a.active[slot];
   if (io < 0 || io >= a.N) {
@@ -387,9 +448,19 @@ __device__ __forceinline__ void adjoint_receiver(const AdjArgs& g, int64_t slot,
     const int n = min(total - lo, a.M);
     if (n > 0) {
       bin_sources(a, lane, U, Up, n, V, off);
+      // bin_sources leaves the beams in Up unsorted: put them in V's order
+      for (int e = lane; e < a.npix; e += 32) {
+        const int s0 = e ? off[e - 1] : 0, s1 = off[e];
+        for (int j = s0; j < s1; ++j) Up[j] = e;
+      }
       if (lane == 0) *next_beam = 32;
       __syncwarp();
-      absorb_adjoint<NBP>(g, x, si, lane, lstk, V, Q, S, off, next_beam, gJf, Js, Jc);
+      adjoint_stage1<NBP>(g, x, si, lane, lstk, V, T, Q, S, off, binfo, next_beam);
+      __syncwarp();
+      adjoint_stage2<NBP>(g, x, si, lane, V, Up, T, Q, n, gJf, Js, Jc);
+      if (lane == 0) *next_beam = 32;
+      __syncwarp();
+      adjoint_stage3<NBP>(g, x, si, lane, lstk, V, Q, S, off, binfo, next_beam);
       __syncwarp();
     }
     if (lo + a.M >= total) break;
@@ -410,20 +481,28 @@ __device__ __forceinline__ void adjoint_receiver(const AdjArgs& g, int64_t slot,
   }
 }
 
+// Shared memory of an adjoint block: per warp the stacks, the beam offsets,
+// the beam records and the next-beam counter.
+inline size_t adjoint_smem(int warps, int stack_ints, int npix) {
+  return size_t(warps) * (stack_ints + 2 * npix + 1) * sizeof(int);
+}
+
 template <int NBP, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_walk_adjoint(const __grid_constant__ AdjArgs g) {
   extern __shared__ int smem[];
   const WalkArgs& a = g.w;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;
-  int* wsm = smem + wib * (a.stack_ints + a.npix + 1);
+  int* wsm = smem + wib * (a.stack_ints + 2 * a.npix + 1);
   int* stk = wsm;
   int* off = wsm + a.stack_ints;
-  int* next_beam = off + a.npix;
+  uint32_t* binfo = reinterpret_cast<uint32_t*>(off + a.npix);
+  int* next_beam = off + 2 * a.npix;
   int* lstk = stk + lane * (a.max_depth + 2);
   SrcEntry* U = a.srcU + gw * a.M;
   int* Up = a.pixU + gw * a.M;
   SrcEntry* V = a.srcV + gw * a.M;
+  float* T = g.T + gw * a.M * NBP;
   float* Q = g.Q + gw * a.M * NBP;
   float4* S = g.seg + gw * g.seg_cap * 32;
   for (;;) {
@@ -431,7 +510,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_walk_adjoint(const __grid_consta
     if (lane == 0) slot = atomicAdd(a.counter, 1ull);
     slot = __shfl_sync(0xffffffffu, slot, 0);
     if (slot >= (unsigned long long)a.A) break;
-    adjoint_receiver<NBP>(g, int64_t(slot), lane, stk, off, next_beam, lstk, U, Up, V, Q, S);
+    adjoint_receiver<NBP>(g, int64_t(slot), lane, stk, off, binfo, next_beam, lstk, U, Up, V, T, Q,
+                          S);
   }
 }
 
@@ -501,7 +581,7 @@ __global__ void k_grad_elements(int64_t N, int nb, double inv_size2, const int* 
                                 const int* __restrict__ depth, const float* __restrict__ mass,
                                 const double* __restrict__ pos64, const float4* __restrict__ csrc,
                                 const double* __restrict__ c64, const float* __restrict__ g_aleaf,
-                                const float* __restrict__ g_Lnode, const float* __restrict__ g_c,
+                                const float* __restrict__ g_Lnode, const float4* __restrict__ g_c,
                                 const float* __restrict__ g_Lelem, const float* __restrict__ g_thick,
                                 float* __restrict__ g_kappa, float* __restrict__ g_lum) {
   const int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -521,7 +601,9 @@ __global__ void k_grad_elements(int64_t N, int nb, double inv_size2, const int* 
     const float Lt = csrc[q].w;
     if (Lt > 0.0f) {
       double dot = 0.0;
-      for (int a = 0; a < 3; ++a) dot += double(g_c[3 * int64_t(q) + a]) * (x[a] - c64[3 * int64_t(q) + a]);
+      const float4 gc = g_c[q];
+      const double gcv[3] = {double(gc.x), double(gc.y), double(gc.z)};
+      for (int a = 0; a < 3; ++a) dot += gcv[a] * (x[a] - c64[3 * int64_t(q) + a]);
       dot /= double(Lt);
 #pragma unroll
       for (int b = 0; b < NBP; ++b) gl[b] += dot;
@@ -606,7 +688,7 @@ extern "C" int trevr2_J_backward(trevr2_tree* tree, const int64_t* active, int64
   wa.A = A;
   wa.active = active;
   const void* fn = nbp == 1 ? adjoint_kernel<1>() : nbp == 2 ? adjoint_kernel<2>() : adjoint_kernel<4>();
-  const size_t smem = walk_smem(kAdjWarps, wa.stack_ints, wa.npix);
+  const size_t smem = adjoint_smem(kAdjWarps, wa.stack_ints, wa.npix);
   int per_sm = 0, sms = 0;
   T2_CHECK(config_walk_kernel(fn, kAdjWarps, smem, &per_sm, &sms));
   int64_t blocks = int64_t(sms) * per_sm;
@@ -618,12 +700,13 @@ extern "C" int trevr2_J_backward(trevr2_tree* tree, const int64_t* active, int64
   const size_t b_atab = up(sizeof(float) * size_t(std::max<int64_t>(t->n_internal, 1)) * P * nbp);
   const size_t b_aleaf = up(sizeof(float) * size_t(n) * nbp);
   const size_t b_Lnode = b_aleaf;
-  const size_t b_c = up(sizeof(float) * size_t(n) * 3);
+  const size_t b_c = up(sizeof(float4) * size_t(n));
   const size_t b_Lelem = up(sizeof(float) * size_t(N) * nbp);
   const size_t b_thick = b_Lelem;
   const size_t zeroed = b_atab + b_aleaf + b_Lnode + b_c + b_Lelem + b_thick;
   const size_t b_leaf = up(sizeof(int) * size_t(std::max<int64_t>(N, 1)));
   const size_t b_Q = up(sizeof(float) * warps * wa.M * nbp);
+  const size_t b_T = b_Q;
   // segment records address the table by a 32-bit row index
   const int seg_cap = int64_t(std::max<int64_t>(t->n_internal, 1)) * P < INT32_MAX ? kSegCap : 0;
   const size_t b_seg = up(sizeof(float4) * warps * size_t(seg_cap) * 32);
@@ -631,7 +714,7 @@ extern "C" int trevr2_J_backward(trevr2_tree* tree, const int64_t* active, int64
   char* base = nullptr;
   {
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base),
-                                    zeroed + b_leaf + b_Q + b_seg + b_walk, st);
+                                    zeroed + b_leaf + b_T + b_Q + b_seg + b_walk, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(adjoint buffers)");
   }
   AdjArgs g;
@@ -642,10 +725,11 @@ extern "C" int trevr2_J_backward(trevr2_tree* tree, const int64_t* active, int64
   g.g_atab = reinterpret_cast<float*>(p); p += b_atab;
   g.g_aleaf = reinterpret_cast<float*>(p); p += b_aleaf;
   g.g_Lnode = reinterpret_cast<float*>(p); p += b_Lnode;
-  g.g_c = reinterpret_cast<float*>(p); p += b_c;
+  g.g_c = reinterpret_cast<float4*>(p); p += b_c;
   g.g_Lelem = reinterpret_cast<float*>(p); p += b_Lelem;
   g.g_thick = reinterpret_cast<float*>(p); p += b_thick;
   int* leaf_of = reinterpret_cast<int*>(p); p += b_leaf;
+  g.T = reinterpret_cast<float*>(p); p += b_T;
   g.Q = reinterpret_cast<float*>(p); p += b_Q;
   g.seg = reinterpret_cast<float4*>(p); p += b_seg;
   g.seg_cap = seg_cap;

@@ -47,6 +47,7 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
     int ptr = k ? off[k - 1] : 0;
     const int end = off[k];
     const float smax = V[end - 1].s;
+    float s_next = V[ptr].s;  // the nearest source not yet passed
     const float4 dn = a.dirs[k];
     const int pair = __float_as_int(dn.w);
     const float n[3] = {dn.x, dn.y, dn.z};
@@ -82,7 +83,9 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
       if (!(nd.meta & kMetaLeaf) && cell_opens(a, q, nd, x, si)) {
         // the crossed halves, the near one (the side of the receiver) on top
         bool lower_first, lower_hit, upper_hit;
-        crossed_halves(nd, xv, n, inv, t0, t1, lower_first, lower_hit, upper_hit);
+        float lt0, lt1, ut0, ut1;
+        crossed_halves(nd, xv, n, inv, t0, t1, lower_first, lower_hit, upper_hit, lt0, lt1, ut0,
+                       ut1);
         const bool near_hit = lower_first ? lower_hit : upper_hit;
         const bool far_hit = lower_first ? upper_hit : lower_hit;
         if (far_hit) lstk[sp++] = lower_first ? nd.child + 1 : nd.child;
@@ -92,15 +95,14 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
       const BandVec<NBP> al = (nd.meta & kMetaLeaf)
                                   ? load_bands<NBP>(a.alpha_leaf + int64_t(q) * NBP)
                                   : load_bands<NBP>(a.alpha_tab + (int64_t(nd.aux) * a.P + pair) * NBP);
-      while (ptr < end) {
-        const float s_ = V[ptr].s;
-        if (!(s_ < t1)) break;
-        const float ds = fmaxf(0.0f, s_ - t0);
+      while (s_next < t1) {
+        const float ds = fmaxf(0.0f, s_next - t0);
         BandVec<NBP> tk;
 #pragma unroll
         for (int b = 0; b < NBP; ++b) tk.v[b] = tau[b] + al.v[b] * ds;
         store_bands<NBP>(T + int64_t(ptr) * NBP, tk);
         ++ptr;
+        s_next = ptr < end ? V[ptr].s : INFINITY;
       }
 #pragma unroll
       for (int b = 0; b < NBP; ++b) tau[b] += al.v[b] * (t1 - t0);

@@ -67,14 +67,16 @@ __device__ __forceinline__ float3 node_ext(uint32_t meta) {
 }
 
 // The halves of an opened node that a beam (x + t n, t in [t0, t1), the
-// node's own chord) crosses and that hold some absorption, and which half
-// the beam meets first (the receiver's side).  The crossing time of the
-// split plane is the face time each half computes for itself, so a half is
-// reported crossed exactly when its own chord test would find t0 < t1.
+// node's own chord) crosses and that hold some absorption, which half the
+// beam meets first (the receiver's side), and each half's chord [lt0, lt1),
+// [ut0, ut1).  The crossing time of the split plane is the face time each
+// half computes for itself and min/max are exact, so these are bit for bit
+// the chords the halves' own slab tests give.
 __device__ __forceinline__ void crossed_halves(const NodeW& nd, const float xv[3], const float n[3],
                                                const float inv[3], float t0, float t1,
                                                bool& lower_first, bool& lower_hit,
-                                               bool& upper_hit) {
+                                               bool& upper_hit, float& lt0, float& lt1,
+                                               float& ut0, float& ut1) {
   const int axis = int(nd.meta & kMetaDepthMask) % 3;
   const float3 e = node_ext(nd.meta);
   const float lo = axis == 0 ? nd.lo[0] : (axis == 1 ? nd.lo[1] : nd.lo[2]);
@@ -84,14 +86,23 @@ __device__ __forceinline__ void crossed_halves(const NodeW& nd, const float xv[3
   const float ia = axis == 0 ? inv[0] : (axis == 1 ? inv[1] : inv[2]);
   const float mid = lo + 0.5f * ex;
   lower_first = xa < mid;
+  lt0 = ut0 = t0;
+  lt1 = ut1 = t1;
   if (na == 0.0f) {
     lower_hit = lower_first;
     upper_hit = !lower_first;
   } else {
     const float tm = (mid - xa) * ia;
-    const bool first = t0 < fminf(t1, tm), second = fmaxf(t0, tm) < t1;
-    lower_hit = na > 0.0f ? first : second;
-    upper_hit = na > 0.0f ? second : first;
+    const float a1 = fminf(t1, tm), b0 = fmaxf(t0, tm);  // [t0, a1) before, [b0, t1) after
+    if (na > 0.0f) {
+      lt1 = a1;
+      ut0 = b0;
+    } else {
+      ut1 = a1;
+      lt0 = b0;
+    }
+    lower_hit = lt0 < lt1;
+    upper_hit = ut0 < ut1;
   }
   lower_hit &= (nd.meta & kMetaChild0Alpha) != 0;
   upper_hit &= (nd.meta & kMetaChild1Alpha) != 0;
