@@ -62,6 +62,9 @@ struct AdjArgs {
 // Segments recorded front to back, replayed back to front: per lane and pass.
 constexpr int kSegCap = 128;
 constexpr int kAdjWarps = 8;  // warps per block of the adjoint walk
+// Blocks per SM it is compiled for (80 registers): measured faster than 2
+// blocks at 120 registers and than 7 blocks of 4 warps at 72.
+constexpr int kAdjBlocksPerSM = 3;
 // Beam record in shared memory: recording lane (5 bits), first record
 // (13 bits), count (14 bits); kBeamRewalk marks a beam whose records did not fit.
 constexpr uint32_t kBeamRewalk = 0x3fffu;
@@ -488,7 +491,7 @@ inline size_t adjoint_smem(int warps, int stack_ints, int npix) {
 }
 
 template <int NBP, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_walk_adjoint(const __grid_constant__ AdjArgs g) {
+__global__ void __launch_bounds__(WARPS * 32, kAdjBlocksPerSM) k_walk_adjoint(const __grid_constant__ AdjArgs g) {
   extern __shared__ int smem[];
   const WalkArgs& a = g.w;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
