@@ -178,7 +178,11 @@ int trevr2_J_backward(trevr2_tree* tree, const int64_t* active, int64_t A, int n
  * launch: subsets s = 0..nsub-1 are concatenated, subset s owning rows
  * offsets[s] <= r < offsets[s+1] of `active` and of J, and walked in tree
  * trees[tree_of[s]].  Each row equals what trevr2_J gives for the same tree,
- * receiver, nside, theta and flags (all nb bands, in band order).
+ * receiver, nside, theta and flags (all nb bands, in band order), bit for
+ * bit.  Rows asking for the same receiver of the same tree (in one subset or
+ * in several) are walked once and copied: a run sorts the rows by (tree,
+ * receiver position in the tree's Morton order), walks the distinct ones in
+ * that order and scatters the results.
  */
 typedef struct trevr2_batch trevr2_batch;
 
@@ -195,19 +199,22 @@ typedef struct trevr2_batch trevr2_batch;
  *  nside, theta, flags   as for trevr2_J (TREVR2_ASYNC is ignored here)
  *  out      receives the plan.  Creation builds any missing alpha tables of
  *           the trees for `nside`, copies offsets/tree_of to the device and
- *           allocates the walk buffers of the default launch shape.  It
- *           synchronises `stream`.
+ *           allocates the walk buffers of the default launch shape and the
+ *           deduplication buffers (about 24 + 4 nb bytes per row plus a sort
+ *           workspace of about 12 bytes per row).  It synchronises `stream`.
  * Errors: EINVAL (NULL arrays, mismatched band counts, bad offsets or
- * tree_of, bad nside/theta/flags), EUNSUPPORTED (too many trees, nside > 16,
- * shared memory exceeded by the deepest tree), ENOMEM, ECUDA.
+ * tree_of, bad nside/theta/flags), EUNSUPPORTED (too many trees, 2^31 rows or
+ * more, nside > 16, shared memory exceeded by the deepest tree), ENOMEM,
+ * ECUDA.
  */
 int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const int64_t* offsets,
                         const int* tree_of, int nsub, int nside, float theta, uint32_t flags,
                         void* stream, trevr2_batch** out);
 
 /*
- * trevr2_batch_run — enqueues the whole batch: one memset of the work
- * counter and one kernel launch, with no allocation and no synchronisation.
+ * trevr2_batch_run — enqueues the whole batch: a fixed sequence of kernels
+ * (row keys, radix sort, distinct keys, walk, scatter) on `stream`, with no
+ * allocation and no synchronisation, so it can be recorded in a CUDA graph.
  *  active  [offsets[nsub]] int64 receiver indices (each in its subset's tree)
  *  J       [offsets[nsub]][nb] float32 output, overwritten
  * Does not synchronise; trevr2_batch_status reports device errors (indices

@@ -98,28 +98,37 @@ __global__ void k_scan_total(const int* scanned, const int* orig_last, int64_t n
 
 __global__ void k_copy_last(const int* d, int64_t n, int* out) { *out = n ? d[n - 1] : 0; }
 
-int scan_exclusive_i32(int* d, int64_t n, int* d_total, cudaStream_t st) {
-  int* last = nullptr;
-  T2_CHECK(dalloc(&last, 1, st));
+size_t scan_ws_ints(int64_t n) {
+  const int64_t nblocks = (n + kScanItems - 1) / kScanItems;
+  return 1 + (nblocks > 1 ? size_t(nblocks) + scan_ws_ints(nblocks) : 0);
+}
+
+// ws: the last input value, then the block sums of each recursion level.
+static int scan_with_ws(int* d, int64_t n, int* d_total, cudaStream_t st, int* ws) {
+  int* last = ws;
   k_copy_last<<<1, 1, 0, st>>>(d, n, last); note_launch();
   if (n > 0) {
     int64_t nblocks = (n + kScanItems - 1) / kScanItems;
     if (nblocks == 1) {
       k_scan_block<<<1, kScanThreads, 0, st>>>(d, n, nullptr); note_launch();
     } else {
-      int* sums = nullptr;
-      T2_CHECK(dalloc(&sums, nblocks, st));
+      int* sums = ws + 1;
       k_scan_block<<<unsigned(nblocks), kScanThreads, 0, st>>>(d, n, sums); note_launch();
-      int rc = scan_exclusive_i32(sums, nblocks, nullptr, st);
-      if (rc != TREVR2_OK) return rc;
+      T2_CHECK(scan_with_ws(sums, nblocks, nullptr, st, sums + nblocks));
       k_scan_add<<<unsigned(nblocks), 256, 0, st>>>(d, n, sums); note_launch();
-      dfree(sums, st);
     }
   }
   if (d_total) k_scan_total<<<1, 1, 0, st>>>(d, last, n, d_total); note_launch();
-  dfree(last, st);
   T2_CUDA(cudaGetLastError());
   return TREVR2_OK;
+}
+
+int scan_exclusive_i32(int* d, int64_t n, int* d_total, cudaStream_t st, int* ws) {
+  if (ws) return scan_with_ws(d, n, d_total, st, ws);
+  T2_CHECK(dalloc(&ws, scan_ws_ints(n), st));
+  const int rc = scan_with_ws(d, n, d_total, st, ws);
+  dfree(ws, st);
+  return rc;
 }
 
 // ---------------------------------------------------------------------------
@@ -185,30 +194,47 @@ __global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const int* __r
   }
 }
 
-int radix_sort_u64_i32(uint64_t* keys, int* vals, int64_t n, cudaStream_t st, int key_bits) {
+size_t radix_ws_bytes(int64_t n) {
+  const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+  auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+  return up(sizeof(uint64_t) * size_t(n)) + up(sizeof(int) * size_t(n)) +
+         up(sizeof(int) * 256 * size_t(ntiles)) + up(sizeof(int) * scan_ws_ints(256 * ntiles));
+}
+
+int radix_sort_u64_i32(uint64_t* keys, int* vals, int64_t n, cudaStream_t st, int key_bits,
+                       void* ws) {
   if (n <= 1) return TREVR2_OK;
   // an even number of 8-bit passes, so the result ends in the caller's buffers
   int passes = (std::min(std::max(key_bits, 1), 64) + 7) / 8;
   passes += passes & 1;
   const int ntiles = int((n + kSortTile - 1) / kSortTile);
-  uint64_t* k2 = nullptr;
-  int* v2 = nullptr;
-  int* hist = nullptr;
-  T2_CHECK(dalloc(&k2, n, st));
-  T2_CHECK(dalloc(&v2, n, st));
-  T2_CHECK(dalloc(&hist, size_t(256) * ntiles, st));
+  const bool own = ws == nullptr;
+  if (own) {
+    cudaError_t e = cudaMallocAsync(&ws, radix_ws_bytes(n), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(sort workspace)");
+  }
+  auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+  char* p = static_cast<char*>(ws);
+  uint64_t* k2 = reinterpret_cast<uint64_t*>(p);
+  p += up(sizeof(uint64_t) * size_t(n));
+  int* v2 = reinterpret_cast<int*>(p);
+  p += up(sizeof(int) * size_t(n));
+  int* hist = reinterpret_cast<int*>(p);
+  p += up(sizeof(int) * 256 * size_t(ntiles));
+  int* scan_ws = reinterpret_cast<int*>(p);
   uint64_t *ka = keys, *kb = k2;
   int *va = vals, *vb = v2;
-  for (int shift = 0; shift < 8 * passes; shift += 8) {
+  int rc = TREVR2_OK;
+  for (int shift = 0; shift < 8 * passes && rc == TREVR2_OK; shift += 8) {
     k_radix_hist<<<ntiles, kSortThreads, 0, st>>>(ka, n, shift, hist, ntiles); note_launch();
-    T2_CHECK(scan_exclusive_i32(hist, int64_t(256) * ntiles, nullptr, st));
+    rc = scan_exclusive_i32(hist, int64_t(256) * ntiles, nullptr, st, scan_ws);
+    if (rc != TREVR2_OK) break;
     k_radix_scatter<<<ntiles, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, hist, ntiles); note_launch();
     std::swap(ka, kb);
     std::swap(va, vb);
   }
-  dfree(k2, st);
-  dfree(v2, st);
-  dfree(hist, st);
+  if (own) cudaFreeAsync(ws, st);
+  if (rc != TREVR2_OK) return rc;
   T2_CUDA(cudaGetLastError());
   return TREVR2_OK;
 }

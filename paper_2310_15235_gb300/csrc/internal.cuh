@@ -163,10 +163,15 @@ void dfree(T*& p, cudaStream_t st) {
 }
 
 // Exclusive scan of n int32 values in place; *d_total (device) gets the sum.
-int scan_exclusive_i32(int* d, int64_t n, int* d_total, cudaStream_t st);
+// ws (device, scan_ws_ints(n) ints) or NULL to allocate one stream ordered.
+size_t scan_ws_ints(int64_t n);
+int scan_exclusive_i32(int* d, int64_t n, int* d_total, cudaStream_t st, int* ws = nullptr);
 
 // Stable LSD radix sort of keys below 2^key_bits with int32 payload (in place).
-int radix_sort_u64_i32(uint64_t* keys, int* vals, int64_t n, cudaStream_t st, int key_bits = 64);
+// ws (device, radix_ws_bytes(n) bytes) or NULL to allocate one stream ordered.
+size_t radix_ws_bytes(int64_t n);
+int radix_sort_u64_i32(uint64_t* keys, int* vals, int64_t n, cudaStream_t st, int key_bits = 64,
+                       void* ws = nullptr);
 
 // Alpha tables and beam directions for one nside (built and cached).
 int ensure_table(Tree* t, int nside, cudaStream_t st, Table** out);

@@ -141,15 +141,9 @@ __device__ __forceinline__ void eval_sources(const WalkArgs& a, int lane, const 
 // J of one receiver (caller index io of the tree described by a) into
 // Jrow[0, nbsel); the warp's shared stacks and buffers are passed in.
 template <int NBP>
-__device__ __forceinline__ void walk_receiver(const WalkArgs& a, int64_t io, float* Jrow, int lane,
-                                              int* stk, int* off, int* next_beam, int* lstk,
-                                              SrcEntry* U, int* Up, SrcEntry* V, float* T) {
-  if (io < 0 || io >= a.N) {
-    if (lane == 0) atomicOr(a.status, kStatusBadActive);
-    if (lane < a.nbsel) Jrow[lane] = __int_as_float(0x7fc00000);
-    return;
-  }
-  const int si = a.inv[io];
+__device__ __forceinline__ void walk_receiver_si(const WalkArgs& a, int si, float* Jrow, int lane,
+                                                 int* stk, int* off, int* next_beam, int* lstk,
+                                                 SrcEntry* U, int* Up, SrcEntry* V, float* T) {
   const float4 xr = a.pos32[si];
   // the receiver in FP32, on the FP64 side of every box face
   const float3 x = grazing_coords(a, si, make_float3(xr.x, xr.y, xr.z));
@@ -196,6 +190,20 @@ __device__ __forceinline__ void walk_receiver(const WalkArgs& a, int64_t io, flo
   }
 }
 
+// The same for the receiver with caller index io (NaN row and a status bit
+// for an index outside [0, N)).
+template <int NBP>
+__device__ __forceinline__ void walk_receiver(const WalkArgs& a, int64_t io, float* Jrow, int lane,
+                                              int* stk, int* off, int* next_beam, int* lstk,
+                                              SrcEntry* U, int* Up, SrcEntry* V, float* T) {
+  if (io < 0 || io >= a.N) {
+    if (lane == 0) atomicOr(a.status, kStatusBadActive);
+    if (lane < a.nbsel) Jrow[lane] = __int_as_float(0x7fc00000);
+    return;
+  }
+  walk_receiver_si<NBP>(a, a.inv[io], Jrow, lane, stk, off, next_beam, lstk, U, Up, V, T);
+}
+
 // One warp per receiver, receivers from a global counter.
 template <int NBP, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk(WalkArgs a) {
@@ -216,26 +224,40 @@ __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk(Wa
     if (lane == 0) slot = atomicAdd(a.counter, 1ull);
     slot = __shfl_sync(0xffffffffu, slot, 0);
     if (slot >= (unsigned long long)a.A) break;
-    walk_receiver<NBP>(a, a.active[slot], a.J + int64_t(slot) * a.nbsel, lane, stk, off, next_beam,
+    const int64_t r = a.order ? int64_t(a.order[slot]) : int64_t(slot);
+    walk_receiver<NBP>(a, a.active[r], a.J + r * a.nbsel, lane, stk, off, next_beam,
                        lstk, U, Up, V, T);
   }
 }
 
 // Many receiver subsets over several trees in one launch (individual
-// timesteps over independent snapshots, Sec. 1.2 and Sec. 3.1): receiver r
-// of the concatenated list belongs to the subset s with
-// offsets[s] <= r < offsets[s + 1] and is walked in tree tree_of[s].
+// timesteps over independent snapshots, Sec. 1.2 and Sec. 3.1): row r of the
+// concatenated list belongs to the subset s with offsets[s] <= r <
+// offsets[s + 1] and is walked in tree tree_of[s].  Rows that ask for the
+// same receiver of the same tree get the same J, so a run walks every
+// distinct (tree, receiver) once, in the tree's Morton order, and copies the
+// row: keys (tree, element position in the tree), sorted with their rows,
+// first of each key marked and numbered by a scan, the distinct keys walked,
+// the results scattered back.
 constexpr int kMaxBatchTrees = TREVR2_MAX_BATCH_TREES;
 
 struct BatchArgs {
   WalkArgs tree[kMaxBatchTrees];  // per-tree arguments (their active/J fields unused)
+  int ntrees;
+  int key_shift;                  // key = tree << key_shift | element position
   const int64_t* active;          // [total] concatenated receiver indices
   const int64_t* offsets;         // [nsub + 1]
   const int* tree_of;             // [nsub]
   int nsub;
-  int64_t total;
+  int64_t total;                  // rows of this run
   float* J;                       // [total][nbsel]
   int nbsel;
+  uint64_t* keys;                 // [total] keys of the rows, sorted
+  int* rows;                      // [total] row of each sorted key
+  int* first_scan;                // [total] distinct keys before each sorted key
+  uint64_t* ukeys;                // [distinct] the distinct keys
+  float* Ju;                      // [distinct][nbsel] J of each distinct key
+  int* n_distinct;                // device count of distinct keys
   SrcEntry* srcU;
   int* pixU;
   SrcEntry* srcV;
@@ -247,6 +269,56 @@ struct BatchArgs {
   unsigned long long* counter;
 };
 
+// Key of every row: its tree and the receiver's position in that tree's
+// element order; invalid receivers get tree = ntrees (sorted last, one key
+// per row) and their tree's status bit.
+__global__ void k_batch_keys(const __grid_constant__ BatchArgs B) {
+  const int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (r >= B.total) return;
+  int lo = 0, hi = B.nsub;  // offsets[lo] <= r < offsets[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (B.offsets[mid] <= r) lo = mid; else hi = mid;
+  }
+  const int t = B.tree_of[lo];
+  const WalkArgs& a = B.tree[t];
+  const int64_t io = B.active[r];
+  if (io >= 0 && io < a.N) {
+    B.keys[r] = (uint64_t(t) << B.key_shift) | uint64_t(uint32_t(a.inv[io]));
+  } else {
+    B.keys[r] = uint64_t(B.ntrees) << B.key_shift;
+    atomicOr(a.status, kStatusBadActive);
+  }
+  B.rows[r] = int(r);
+}
+
+__device__ __forceinline__ bool first_of_key(const uint64_t* keys, int64_t p) {
+  return p == 0 || keys[p] != keys[p - 1];
+}
+
+__global__ void k_batch_first(const __grid_constant__ BatchArgs B) {
+  const int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (p < B.total) B.first_scan[p] = first_of_key(B.keys, p) ? 1 : 0;
+}
+
+__global__ void k_batch_distinct(const __grid_constant__ BatchArgs B) {
+  const int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (p < B.total && first_of_key(B.keys, p)) B.ukeys[B.first_scan[p]] = B.keys[p];
+}
+
+// Every row gets its key's J (NaN for an invalid receiver).
+__global__ void k_batch_scatter(const __grid_constant__ BatchArgs B) {
+  const int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (p >= B.total) return;
+  const uint64_t key = B.keys[p];
+  const int64_t r = B.rows[p];
+  const int64_t u = B.first_scan[p] - (first_of_key(B.keys, p) ? 0 : 1);
+  const bool ok = int(key >> B.key_shift) < B.ntrees;
+  for (int j = 0; j < B.nbsel; ++j)
+    B.J[r * B.nbsel + j] = ok ? B.Ju[u * B.nbsel + j] : __int_as_float(0x7fc00000);
+}
+
+// One warp per distinct valid key, keys from a global counter.
 template <int NBP, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk_batched(const __grid_constant__ BatchArgs B) {
   extern __shared__ int smem[];
@@ -261,25 +333,18 @@ __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk_ba
   int* Up = B.pixU + gw * B.M;
   SrcEntry* V = B.srcV + gw * B.M;
   float* T = B.srcT + gw * B.M * 4;
+  const unsigned long long nd = (unsigned long long)(*B.n_distinct);
   for (;;) {
-    unsigned long long r = 0;
-    int t = 0;
-    if (lane == 0) {
-      r = atomicAdd(B.counter, 1ull);
-      if (r < (unsigned long long)B.total) {
-        int lo = 0, hi = B.nsub;  // offsets[lo] <= r < offsets[hi]
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (B.offsets[mid] <= int64_t(r)) lo = mid; else hi = mid;
-        }
-        t = B.tree_of[lo];
-      }
-    }
-    r = __shfl_sync(0xffffffffu, r, 0);
-    t = __shfl_sync(0xffffffffu, t, 0);
-    if (r >= (unsigned long long)B.total) break;
-    walk_receiver<NBP>(B.tree[t], B.active[r], B.J + int64_t(r) * B.nbsel, lane, stk, off,
-                       next_beam, lstk, U, Up, V, T);
+    unsigned long long u = 0;
+    if (lane == 0) u = atomicAdd(B.counter, 1ull);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= nd) break;
+    const uint64_t key = B.ukeys[u];
+    const int t = int(key >> B.key_shift);
+    if (t >= B.ntrees) break;  // invalid receivers sort last
+    const int si = int(key & ((uint64_t(1) << B.key_shift) - 1));
+    walk_receiver_si<NBP>(B.tree[t], si, B.Ju + int64_t(u) * B.nbsel, lane, stk, off, next_beam,
+                          lstk, U, Up, V, T);
   }
 }
 
@@ -375,6 +440,16 @@ static void place_walk_buffers(char* base, size_t warps, int M, SrcEntry** U, Sr
   *Up = reinterpret_cast<int*>(base + 2 * warps * M * sizeof(SrcEntry) + warps * M * 4 * sizeof(float));
 }
 
+__global__ void k_order_keys(const int64_t* __restrict__ active, int64_t A, int64_t N,
+                             const int* __restrict__ inv, uint64_t* __restrict__ keys,
+                             int* __restrict__ slots) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= A) return;
+  const int64_t io = active[i];
+  keys[i] = (io >= 0 && io < N) ? uint64_t(inv[io]) : uint64_t(N);
+  slots[i] = int(i);
+}
+
 static int launch_walk(Tree* t, Table* tb, const int64_t* active, int64_t A, int nside,
                        float theta, const int* bsel, int nbsel, uint32_t flags, float* J,
                        cudaStream_t st) {
@@ -383,6 +458,25 @@ static int launch_walk(Tree* t, Table* tb, const int64_t* active, int64_t A, int
   a.active = active;
   a.A = A;
   a.J = J;
+  if (A > 1) {
+    const size_t need = size_t(A) * (sizeof(uint64_t) + sizeof(int));
+    if (t->order_bytes < need) {
+      if (t->order_buf) cudaFreeAsync(t->order_buf, st);
+      t->order_buf = nullptr;
+      t->order_bytes = 0;
+      cudaError_t e = cudaMallocAsync(&t->order_buf, need, st);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(receiver order)");
+      t->order_bytes = need;
+    }
+    uint64_t* keys = static_cast<uint64_t*>(t->order_buf);
+    int* slots = reinterpret_cast<int*>(keys + A);
+    k_order_keys<<<unsigned((A + 255) / 256), 256, 0, st>>>(active, A, t->N, t->inv, keys, slots);
+    note_launch();
+    int bits = 1;
+    while ((int64_t(1) << bits) <= t->N) ++bits;
+    T2_CHECK(radix_sort_u64_i32(keys, slots, A, st, bits));
+    a.order = slots;
+  }
   const void* fn = walk_kernel(t->nbp, kWalkWarps, false);
   const size_t smem = walk_smem(kWalkWarps, a.stack_ints, a.npix);
   int per_sm = 0, sms = 0;
@@ -496,6 +590,10 @@ struct Batch {
   unsigned long long* counter = nullptr;
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  void* dedup = nullptr;     // keys, rows, scan, distinct keys, their J, sort workspace
+  void* sort_ws = nullptr;
+  int* scan_ws = nullptr;
+  int key_bits = 64;
   int warps = kWalkWarps;  // chosen launch shape
   int M = kSrcCapacity;    // chosen source staging depth
   const void* fn = nullptr;  // kernel, shared memory and grid of that shape
@@ -541,16 +639,26 @@ static int batch_select(Batch* b, int warps, int M, int64_t limit, cudaStream_t 
   return TREVR2_OK;
 }
 
-// Enqueues the walk in the selected shape: one memset and one kernel, with
-// no allocation, synchronisation or attribute call, so that it can be
-// recorded into a CUDA graph.
+// Enqueues the run in the selected shape (keys, sort, distinct keys, walk,
+// scatter) with no allocation, synchronisation or attribute call, so that it
+// can be recorded into a CUDA graph.
 static int batch_enqueue(Batch* b, const int64_t* active, float* J, cudaStream_t st) {
   b->args.active = active;
   b->args.J = J;
+  const int64_t R = b->args.total;
+  if (R <= 0) return TREVR2_OK;
+  const unsigned g = unsigned((R + 255) / 256);
   T2_CUDA(cudaMemsetAsync(b->counter, 0, sizeof(unsigned long long), st));
+  k_batch_keys<<<g, 256, 0, st>>>(b->args); note_launch();
+  T2_CHECK(radix_sort_u64_i32(b->args.keys, b->args.rows, R, st, b->key_bits, b->sort_ws));
+  k_batch_first<<<g, 256, 0, st>>>(b->args); note_launch();
+  T2_CHECK(scan_exclusive_i32(b->args.first_scan, R, b->args.n_distinct, st, b->scan_ws));
+  k_batch_distinct<<<g, 256, 0, st>>>(b->args); note_launch();
   void* argv[] = {&b->args};
   T2_CUDA(cudaLaunchKernel(b->fn, dim3(unsigned(b->blocks)), dim3(b->warps * 32), argv, b->smem, st));
   note_launch();
+  k_batch_scatter<<<g, 256, 0, st>>>(b->args); note_launch();
+  T2_CUDA(cudaGetLastError());
   return TREVR2_OK;
 }
 
@@ -560,6 +668,8 @@ static void free_batch(Batch* b, cudaStream_t st) {
   dfree(b->counter, st);
   if (b->scratch) cudaFreeAsync(b->scratch, st);
   b->scratch = nullptr;
+  if (b->dedup) cudaFreeAsync(b->dedup, st);
+  b->dedup = nullptr;
 }
 
 }  // namespace trevr2
@@ -600,6 +710,10 @@ extern "C" int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const 
   if (nsub > 0 && offsets[0] != 0) {
     set_error("trevr2_batch_create: offsets[0] must be 0");
     return TREVR2_EINVAL;
+  }
+  if (nsub > 0 && offsets[nsub] >= (int64_t(1) << 31)) {
+    set_error("trevr2_batch_create: at most 2^31 - 1 rows per batch");
+    return TREVR2_EUNSUPPORTED;
   }
   for (int s = 0; s < nsub; ++s) {
     if (offsets[s + 1] < offsets[s] || tree_of[s] < 0 || tree_of[s] >= ntrees) {
@@ -650,10 +764,36 @@ extern "C" int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const 
   b->args.npix = 12 * nside * nside;
   b->args.nbsel = nb;
   b->args.nsub = nsub;
+  b->args.ntrees = ntrees;
+  int64_t maxN = 1;
+  for (Tree* t : b->trees) maxN = std::max<int64_t>(maxN, t->N);
+  int shift = 1;
+  while ((int64_t(1) << shift) < maxN) ++shift;
+  b->args.key_shift = shift;
+  b->key_bits = shift + 6;  // trees and the invalid marker: at most 33 values
   int rc = dalloc(&b->d_offsets, size_t(nsub) + 1, st);
   if (!rc) rc = dalloc(&b->d_tree_of, size_t(std::max(nsub, 1)), st);
   if (!rc) rc = dalloc(&b->counter, 1, st);
   if (rc) return fail(rc);
+  if (b->total > 0) {
+    // deduplication buffers for all rows, allocated once
+    auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+    const size_t R = size_t(b->total);
+    const size_t bk = up(8 * R), br = up(4 * R), bu = up(4 * R * nb);
+    const size_t bsort = up(radix_ws_bytes(int64_t(R))), bscan = up(4 * scan_ws_ints(int64_t(R)));
+    const size_t bytes = bk * 2 + br * 2 + bu + 256 + bsort + bscan;
+    cudaError_t e = cudaMallocAsync(&b->dedup, bytes, st);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMallocAsync(batch deduplication)"));
+    char* p = static_cast<char*>(b->dedup);
+    b->args.keys = reinterpret_cast<uint64_t*>(p); p += bk;
+    b->args.ukeys = reinterpret_cast<uint64_t*>(p); p += bk;
+    b->args.rows = reinterpret_cast<int*>(p); p += br;
+    b->args.first_scan = reinterpret_cast<int*>(p); p += br;
+    b->args.Ju = reinterpret_cast<float*>(p); p += bu;
+    b->args.n_distinct = reinterpret_cast<int*>(p); p += 256;
+    b->sort_ws = p; p += bsort;
+    b->scan_ws = reinterpret_cast<int*>(p);
+  }
   if (nsub > 0) {
     cudaError_t e = cudaMemcpyAsync(b->d_offsets, offsets, (size_t(nsub) + 1) * sizeof(int64_t),
                                     cudaMemcpyHostToDevice, st);

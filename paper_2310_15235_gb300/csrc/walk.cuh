@@ -36,6 +36,7 @@ struct WalkArgs {
   const float* km;
   const float4* dirs;
   const int64_t* active;
+  const int* order;  // walk order of the receivers (NULL: as given)
   int64_t A;
   int64_t N;
   int nside, npix, P;
