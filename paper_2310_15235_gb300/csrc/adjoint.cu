@@ -199,17 +199,15 @@ __device__ __forceinline__ bool beam_chord(const NodeW& nd, const float xv[3], c
 template <int NBP>
 __device__ void adjoint_stage1(const AdjArgs& g, float3 x, int si, int lane, int* lstk,
                                const SrcEntry* V, float* T, float* Q, float4* S, const int* off,
-                               uint32_t* binfo, int* next_beam) {
+                               const int* order, int nbeams, uint32_t* binfo, int* next_beam) {
   const WalkArgs& a = g.w;
   const float xv[3] = {x.x, x.y, x.z};
   BandVec<NBP> zero;
 #pragma unroll
   for (int b = 0; b < NBP; ++b) zero.v[b] = 0.0f;
   int nrec = 0;
-  int k = lane;
-  for (;;) {
-    while (k < a.npix && (k ? off[k - 1] : 0) == off[k]) k = atomicAdd(next_beam, 1);
-    if (k >= a.npix) break;
+  for (int idx = lane; idx < nbeams; idx = atomicAdd(next_beam, 1)) {
+    const int k = order[idx];
     const int start = k ? off[k - 1] : 0;
     const int end = off[k];
     const float smax = V[end - 1].s;
@@ -282,7 +280,6 @@ __device__ void adjoint_stage1(const AdjArgs& g, float3 x, int si, int lane, int
     }
     const uint32_t count = nrec <= g.seg_cap ? uint32_t(nrec - first) : kBeamRewalk;
     binfo[k] = uint32_t(lane) | ((uint32_t(first) & 0x1fffu) << 5) | (count << 18);
-    k = atomicAdd(next_beam, 1);
   }
 }
 
@@ -347,13 +344,12 @@ __device__ void adjoint_stage2(const AdjArgs& g, float3 x, int si, int lane, con
 template <int NBP>
 __device__ void adjoint_stage3(const AdjArgs& g, float3 x, int si, int lane, int* lstk,
                                const SrcEntry* V, const float* Q, const float4* S, const int* off,
-                               const uint32_t* binfo, int* next_beam) {
+                               const int* order, int nbeams, const uint32_t* binfo,
+                               int* next_beam) {
   const WalkArgs& a = g.w;
   const float xv[3] = {x.x, x.y, x.z};
-  int k = lane;
-  for (;;) {
-    while (k < a.npix && (k ? off[k - 1] : 0) == off[k]) k = atomicAdd(next_beam, 1);
-    if (k >= a.npix) break;
+  for (int idx = lane; idx < nbeams; idx = atomicAdd(next_beam, 1)) {
+    const int k = order[idx];
     const int start = k ? off[k - 1] : 0;
     const int end = off[k];
     const uint32_t info = binfo[k];
@@ -403,7 +399,6 @@ __device__ void adjoint_stage3(const AdjArgs& g, float3 x, int si, int lane, int
         segment_gradient<NBP>(d, t0, t1, V, Q, start, p2, W);
       }
     }
-    k = atomicAdd(next_beam, 1);
   }
 }
 
@@ -456,14 +451,16 @@ __device__ __forceinline__ void adjoint_receiver(const AdjArgs& g, int64_t slot,
         const int s0 = e ? off[e - 1] : 0, s1 = off[e];
         for (int j = s0; j < s1; ++j) Up[j] = e;
       }
+      int* order = reinterpret_cast<int*>(binfo) + a.npix;
+      const int nbeams = order_beams(a, lane, V, off, order, order + a.npix);
       if (lane == 0) *next_beam = 32;
       __syncwarp();
-      adjoint_stage1<NBP>(g, x, si, lane, lstk, V, T, Q, S, off, binfo, next_beam);
+      adjoint_stage1<NBP>(g, x, si, lane, lstk, V, T, Q, S, off, order, nbeams, binfo, next_beam);
       __syncwarp();
       adjoint_stage2<NBP>(g, x, si, lane, V, Up, T, Q, n, gJf, Js, Jc);
       if (lane == 0) *next_beam = 32;
       __syncwarp();
-      adjoint_stage3<NBP>(g, x, si, lane, lstk, V, Q, S, off, binfo, next_beam);
+      adjoint_stage3<NBP>(g, x, si, lane, lstk, V, Q, S, off, order, nbeams, binfo, next_beam);
       __syncwarp();
     }
     if (lo + a.M >= total) break;
@@ -485,9 +482,10 @@ __device__ __forceinline__ void adjoint_receiver(const AdjArgs& g, int64_t slot,
 }
 
 // Shared memory of an adjoint block: per warp the stacks, the beam offsets,
-// the beam records and the next-beam counter.
+// the beam records, the beam order and its 32 bucket counts, the next-beam
+// counter.
 inline size_t adjoint_smem(int warps, int stack_ints, int npix) {
-  return size_t(warps) * (stack_ints + 2 * npix + 1) * sizeof(int);
+  return size_t(warps) * (stack_ints + 3 * npix + 33) * sizeof(int);
 }
 
 template <int NBP, int WARPS>
@@ -496,11 +494,11 @@ __global__ void __launch_bounds__(WARPS * 32, kAdjBlocksPerSM) k_walk_adjoint(co
   const WalkArgs& a = g.w;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;
-  int* wsm = smem + wib * (a.stack_ints + 2 * a.npix + 1);
+  int* wsm = smem + wib * (a.stack_ints + 3 * a.npix + 33);
   int* stk = wsm;
   int* off = wsm + a.stack_ints;
   uint32_t* binfo = reinterpret_cast<uint32_t*>(off + a.npix);
-  int* next_beam = off + 2 * a.npix;
+  int* next_beam = off + 3 * a.npix + 32;  // after the records, the order and its counts
   int* lstk = stk + lane * (a.max_depth + 2);
   SrcEntry* U = a.srcU + gw * a.M;
   int* Up = a.pixU + gw * a.M;

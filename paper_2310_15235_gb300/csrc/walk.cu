@@ -36,14 +36,15 @@
 
 namespace trevr2 {
 
-// Phase A: lanes take beams (those with sources) from a per-warp counter.
+// Phase A: lanes take beams from the order above through a per-warp counter.
 template <int NBP>
 __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int* lstk,
-                             const SrcEntry* V, float* T, const int* off, int* next_beam) {
-  int k = lane;
+                             const SrcEntry* V, float* T, const int* off, const int* order,
+                             int nbeams, int* next_beam) {
+  int idx = lane;
   for (;;) {
-    while (k < a.npix && (k ? off[k - 1] : 0) == off[k]) k = atomicAdd(next_beam, 1);
-    if (k >= a.npix) break;
+    if (idx >= nbeams) break;
+    const int k = order[idx];
     int ptr = k ? off[k - 1] : 0;
     const int end = off[k];
     const float smax = V[end - 1].s;
@@ -112,7 +113,7 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
 #pragma unroll
     for (int b = 0; b < NBP; ++b) tk.v[b] = tau[b];
     for (; ptr < end; ++ptr) store_bands<NBP>(T + int64_t(ptr) * NBP, tk);
-    k = atomicAdd(next_beam, 1);
+    idx = atomicAdd(next_beam, 1);
   }
 }
 
@@ -155,9 +156,11 @@ __device__ __forceinline__ void walk_receiver_si(const WalkArgs& a, int si, floa
     const int n = min(total - lo, a.M);
     if (n > 0) {
       bin_sources(a, lane, U, Up, n, V, off);
+      int* order = off + a.npix;
+      const int nbeams = order_beams(a, lane, V, off, order, order + a.npix);
       if (lane == 0) *next_beam = 32;
       __syncwarp();
-      phase_absorb<NBP>(a, x, si, lane, lstk, V, T, off, next_beam);
+      phase_absorb<NBP>(a, x, si, lane, lstk, V, T, off, order, nbeams, next_beam);
       __syncwarp();
       eval_sources<NBP>(a, lane, V, T, n, Js, Jc);
       __syncwarp();
@@ -210,10 +213,10 @@ __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk(Wa
   extern __shared__ int smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;
-  int* wsm = smem + wib * (a.stack_ints + a.npix + 1);
+  int* wsm = smem + wib * (a.stack_ints + 2 * a.npix + 34);
   int* stk = wsm;
   int* off = wsm + a.stack_ints;
-  int* next_beam = off + a.npix;
+  int* next_beam = off + 2 * a.npix + 32;  // after the beam order and its counts
   int* lstk = stk + lane * (a.max_depth + 2);
   SrcEntry* U = a.srcU + gw * a.M;
   int* Up = a.pixU + gw * a.M;
@@ -324,10 +327,10 @@ __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk_ba
   extern __shared__ int smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;
-  int* wsm = smem + wib * (B.stack_ints + B.npix + 1);
+  int* wsm = smem + wib * (B.stack_ints + 2 * B.npix + 34);
   int* stk = wsm;
   int* off = wsm + B.stack_ints;
-  int* next_beam = off + B.npix;
+  int* next_beam = off + 2 * B.npix + 32;  // after the beam order and its counts
   int* lstk = stk + lane * (B.max_depth + 2);
   SrcEntry* U = B.srcU + gw * B.M;
   int* Up = B.pixU + gw * B.M;

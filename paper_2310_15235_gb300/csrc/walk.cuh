@@ -379,6 +379,37 @@ __device__ __forceinline__ void store_bands(float* p, const BandVec<NBP>& v) {
   }
 }
 
+// The beams that hold sources, farthest source first (longest walks first,
+// so that lanes finish together): a counting sort on 32 log-spaced buckets
+// of the farthest source's distance.  Returns how many there are.
+static __device__ int order_beams(const WalkArgs& a, int lane, const SrcEntry* V, const int* off,
+                           int* order, int* cnt) {
+  cnt[lane] = 0;
+  __syncwarp();
+  for (int k = lane; k < a.npix; k += 32) {
+    const int s0 = k ? off[k - 1] : 0, s1 = off[k];
+    if (s1 > s0) {
+      const int b = min(31, max(0, int(-4.0f * __log2f(V[s1 - 1].s))));
+      atomicAdd(&cnt[b], 1);
+    }
+  }
+  __syncwarp();
+  const int c = cnt[lane];
+  const int incl = warp_incl_scan(c, lane);
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  cnt[lane] = incl - c;
+  __syncwarp();
+  for (int k = lane; k < a.npix; k += 32) {
+    const int s0 = k ? off[k - 1] : 0, s1 = off[k];
+    if (s1 > s0) {
+      const int b = min(31, max(0, int(-4.0f * __log2f(V[s1 - 1].s))));
+      order[atomicAdd(&cnt[b], 1)] = k;
+    }
+  }
+  __syncwarp();
+  return total;
+}
+
 // ---------------------------------------------------------------------------
 // Host side (walk.cu).
 bool valid_nside(int nside);
@@ -392,9 +423,10 @@ int config_walk_kernel(const void* fn, int warps, size_t smem, int* per_sm, int*
 int read_status(Tree* t, cudaStream_t st);
 
 // Per-warp shared memory of a walk block: the traversal stacks, the beam
-// bucket offsets and the next-beam counter.
+// bucket offsets, the beam order and its 32 bucket counts, the next-beam
+// counter.
 inline size_t walk_smem(int warps, int stack_ints, int npix) {
-  return size_t(warps) * (stack_ints + npix + 1) * sizeof(int);
+  return size_t(warps) * (stack_ints + 2 * npix + 34) * sizeof(int);
 }
 
 }  // namespace trevr2
