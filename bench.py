@@ -33,6 +33,11 @@ import workloads  # noqa: E402
 METRIC = "active receiver x HEALPix-ray x band / s"
 UNIT = "receiver*ray*band/s"
 NODE_BYTES = 32  # walk record of one node
+# DRAM bytes (read + write) per receiver of one k_walk launch, from the ncu
+# capture of the 96^3 version of the benchmark field (3.69 GB read + 15.57 GB
+# written for 884,736 receivers); scaled by the receivers of a launch.  It
+# must be measured again (or set to None) whenever the walk kernel changes.
+WALK_TRAFFIC_BYTES_PER_RECEIVER = 21768.0
 
 
 def _workload_name(case):
@@ -292,7 +297,10 @@ def run_ours(args, world, rank, local):
         per_rec, means = _algorithmic_bytes_per_receiver(st, nb)
         achieved = per_rec * A / (walk_avg * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved / hbm_peak, "traffic": None,
+                    "frac": achieved / hbm_peak,
+                    "traffic": (None if WALK_TRAFFIC_BYTES_PER_RECEIVER is None
+                                else WALK_TRAFFIC_BYTES_PER_RECEIVER * A),
+                    "traffic_note": "ncu dram bytes of the 96^3 field scaled by receivers",
                     "kernel": "k_walk", "peak_kind": peak_kind,
                     "algorithmic_bytes_per_unit": per_rec / (npix * nb),
                     "per_receiver_counts": means}
