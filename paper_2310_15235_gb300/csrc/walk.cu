@@ -37,10 +37,16 @@
 namespace trevr2 {
 
 // Phase A: lanes take beams from the order above through a per-warp counter.
+// Each beam first descends the receiver's ancestors (chain[0..], root to the
+// receiver's leaf, in shared memory): they hold the receiver, so they open,
+// and each one's chord is its parent's near-half interval; only their
+// crossed far halves go on the stack.  The stack walk then takes the far
+// halves, nearest first.  This visits the same cells in the same order as a
+// walk from the root.
 template <int NBP>
 __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int* lstk,
                              const SrcEntry* V, float* T, const int* off, const int* order,
-                             int nbeams, int* next_beam) {
+                             int nbeams, int* next_beam, const NodeW* chain, int leaf) {
   int idx = lane;
   for (;;) {
     if (idx >= nbeams) break;
@@ -59,40 +65,8 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
     float tau[NBP];
 #pragma unroll
     for (int b = 0; b < NBP; ++b) tau[b] = 0.0f;
-    int sp = 1;
-    lstk[0] = 0;
-    while (sp > 0 && ptr < end) {
-      const int q = lstk[--sp];
-      const NodeW nd = a.nodes[q];
-      if (!(nd.meta & kMetaHasAlpha)) continue;
-      const float3 e = node_ext(nd.meta);
-      const float ext[3] = {e.x, e.y, e.z};
-      float t0 = 0.0f, t1 = smax;
-      bool hit = true;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float lo = nd.lo[c], hi = lo + ext[c];
-        if (n[c] == 0.0f) {
-          hit &= (lo <= xv[c]) && (xv[c] < hi);  // half-open box for a grazing beam
-        } else {
-          const float ta = (lo - xv[c]) * inv[c], tb = (hi - xv[c]) * inv[c];
-          t0 = fmaxf(t0, fminf(ta, tb));
-          t1 = fminf(t1, fmaxf(ta, tb));
-        }
-      }
-      if (!hit || !(t0 < t1)) continue;
-      if (!(nd.meta & kMetaLeaf) && cell_opens(a, q, nd, x, si)) {
-        // the crossed halves, the near one (the side of the receiver) on top
-        bool lower_first, lower_hit, upper_hit;
-        float lt0, lt1, ut0, ut1;
-        crossed_halves(nd, xv, n, inv, t0, t1, lower_first, lower_hit, upper_hit, lt0, lt1, ut0,
-                       ut1);
-        const bool near_hit = lower_first ? lower_hit : upper_hit;
-        const bool far_hit = lower_first ? upper_hit : lower_hit;
-        if (far_hit) lstk[sp++] = lower_first ? nd.child + 1 : nd.child;
-        if (near_hit) lstk[sp++] = lower_first ? nd.child : nd.child + 1;
-        continue;
-      }
+    // a cell of the cut crossed on [t0, t1): sources inside it, then its tau
+    auto segment = [&](int q, const NodeW& nd, float t0, float t1) {
       const BandVec<NBP> al = (nd.meta & kMetaLeaf)
                                   ? load_bands<NBP>(a.alpha_leaf + int64_t(q) * NBP)
                                   : load_bands<NBP>(a.alpha_tab + (int64_t(nd.aux) * a.P + pair) * NBP);
@@ -107,6 +81,48 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
       }
 #pragma unroll
       for (int b = 0; b < NBP; ++b) tau[b] += al.v[b] * (t1 - t0);
+    };
+    int sp = 0;
+    {
+      const NodeW root = chain[0];
+      float t0, t1;
+      bool go = (root.meta & kMetaHasAlpha) && beam_chord(root, xv, n, inv, smax, t0, t1);
+      for (int kd = 0; go; ++kd) {
+        const NodeW nd = chain[kd];
+        if (nd.meta & kMetaLeaf) {
+          segment(leaf, nd, t0, t1);
+          break;
+        }
+        bool lower_first, lower_hit, upper_hit;
+        float lt0, lt1, ut0, ut1;
+        crossed_halves(nd, xv, n, inv, t0, t1, lower_first, lower_hit, upper_hit, lt0, lt1, ut0,
+                       ut1);
+        const bool near_hit = lower_first ? lower_hit : upper_hit;
+        const bool far_hit = lower_first ? upper_hit : lower_hit;
+        if (far_hit) lstk[sp++] = lower_first ? nd.child + 1 : nd.child;
+        go = near_hit;
+        t0 = lower_first ? lt0 : ut0;
+        t1 = lower_first ? lt1 : ut1;
+      }
+    }
+    while (sp > 0 && ptr < end) {
+      const int q = lstk[--sp];
+      const NodeW nd = a.nodes[q];
+      float t0, t1;
+      if (!beam_chord(nd, xv, n, inv, smax, t0, t1)) continue;
+      if (!(nd.meta & kMetaLeaf) && cell_opens(a, q, nd, x, si)) {
+        // the crossed halves, the near one (the side of the receiver) on top
+        bool lower_first, lower_hit, upper_hit;
+        float lt0, lt1, ut0, ut1;
+        crossed_halves(nd, xv, n, inv, t0, t1, lower_first, lower_hit, upper_hit, lt0, lt1, ut0,
+                       ut1);
+        const bool near_hit = lower_first ? lower_hit : upper_hit;
+        const bool far_hit = lower_first ? upper_hit : lower_hit;
+        if (far_hit) lstk[sp++] = lower_first ? nd.child + 1 : nd.child;
+        if (near_hit) lstk[sp++] = lower_first ? nd.child : nd.child + 1;
+        continue;
+      }
+      segment(q, nd, t0, t1);
     }
     // sources beyond the last absorbing cell of the beam
     BandVec<NBP> tk;
@@ -148,6 +164,23 @@ __device__ __forceinline__ void walk_receiver_si(const WalkArgs& a, int si, floa
   const float4 xr = a.pos32[si];
   // the receiver in FP32, on the FP64 side of every box face
   const float3 x = grazing_coords(a, si, make_float3(xr.x, xr.y, xr.z));
+  // the receiver's ancestors, root first, by the same half-open decisions
+  NodeW* chain = reinterpret_cast<NodeW*>(off + 2 * a.npix + 36);
+  int leaf = 0;
+  {
+    const float xv[3] = {x.x, x.y, x.z};
+    for (int d = 0;; ++d) {
+      const NodeW nd = a.nodes[leaf];
+      if (lane == 0) chain[d] = nd;
+      if (nd.meta & kMetaLeaf) break;
+      bool lower_first, lh, uh;
+      float l0, l1, u0, u1;
+      const float zero3[3] = {0.0f, 0.0f, 0.0f};
+      crossed_halves(nd, xv, zero3, zero3, 0.0f, 1.0f, lower_first, lh, uh, l0, l1, u0, u1);
+      leaf = lower_first ? nd.child : nd.child + 1;
+    }
+    __syncwarp();
+  }
   float Js[NBP], Jc[NBP];
 #pragma unroll
   for (int b = 0; b < NBP; ++b) Js[b] = Jc[b] = 0.0f;
@@ -160,7 +193,7 @@ __device__ __forceinline__ void walk_receiver_si(const WalkArgs& a, int si, floa
       const int nbeams = order_beams(a, lane, V, off, order, order + a.npix);
       if (lane == 0) *next_beam = 32;
       __syncwarp();
-      phase_absorb<NBP>(a, x, si, lane, lstk, V, T, off, order, nbeams, next_beam);
+      phase_absorb<NBP>(a, x, si, lane, lstk, V, T, off, order, nbeams, next_beam, chain, leaf);
       __syncwarp();
       eval_sources<NBP>(a, lane, V, T, n, Js, Jc);
       __syncwarp();
@@ -213,7 +246,7 @@ __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk(Wa
   extern __shared__ int smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;
-  int* wsm = smem + wib * (a.stack_ints + 2 * a.npix + 34);
+  int* wsm = smem + wib * (a.stack_ints + 2 * a.npix + 36 + 8 * (a.max_depth + 1));
   int* stk = wsm;
   int* off = wsm + a.stack_ints;
   int* next_beam = off + 2 * a.npix + 32;  // after the beam order and its counts
@@ -327,7 +360,7 @@ __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk_ba
   extern __shared__ int smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;
-  int* wsm = smem + wib * (B.stack_ints + 2 * B.npix + 34);
+  int* wsm = smem + wib * (B.stack_ints + 2 * B.npix + 36 + 8 * (B.max_depth + 1));
   int* stk = wsm;
   int* off = wsm + B.stack_ints;
   int* next_beam = off + 2 * B.npix + 32;  // after the beam order and its counts
@@ -481,7 +514,7 @@ static int launch_walk(Tree* t, Table* tb, const int64_t* active, int64_t A, int
     a.order = slots;
   }
   const void* fn = walk_kernel(t->nbp, kWalkWarps, false);
-  const size_t smem = walk_smem(kWalkWarps, a.stack_ints, a.npix);
+  const size_t smem = walk_smem(kWalkWarps, a.stack_ints, a.npix, a.max_depth);
   int per_sm = 0, sms = 0;
   T2_CHECK(config_walk_kernel(fn, kWalkWarps, smem, &per_sm, &sms));
   int64_t blocks = int64_t(sms) * per_sm;
@@ -610,7 +643,7 @@ struct Batch {
 static int batch_shape(Batch* b, int warps, int M, int64_t limit, const void** fn, size_t* smem,
                        int64_t* blocks, cudaStream_t st) {
   *fn = walk_kernel(b->nbp, warps, true);
-  *smem = walk_smem(warps, b->args.stack_ints, b->args.npix);
+  *smem = walk_smem(warps, b->args.stack_ints, b->args.npix, b->args.max_depth);
   int per_sm = 0, sms = 0;
   T2_CHECK(config_walk_kernel(*fn, warps, *smem, &per_sm, &sms));
   int64_t g = int64_t(sms) * per_sm;
@@ -1010,7 +1043,7 @@ static int launch_walk_noalloc(Tree* t, Table* tb, const int64_t* active, int64_
   a.A = A;
   a.J = J;
   const void* fn = walk_kernel(t->nbp, kWalkWarps, false);
-  const size_t smem = walk_smem(kWalkWarps, a.stack_ints, a.npix);
+  const size_t smem = walk_smem(kWalkWarps, a.stack_ints, a.npix, a.max_depth);
   int per_sm = 0, sms = 0;
   T2_CHECK(config_walk_kernel(fn, kWalkWarps, smem, &per_sm, &sms));
   // The grid is capped by what the fixed array holds; the kernel loops over

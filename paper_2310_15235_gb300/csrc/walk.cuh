@@ -67,6 +67,30 @@ __device__ __forceinline__ float3 node_ext(uint32_t meta) {
                      __int_as_float((127 - splits_on_axis(d, 2)) << 23));
 }
 
+// Chord [t0, t1) of the beam x + t n (inv = 1/n, 0 where n = 0) with the box
+// of nd, clipped to [0, tmax]; half-open boxes decide grazing beams.
+__device__ __forceinline__ bool beam_chord(const NodeW& nd, const float xv[3], const float n[3],
+                                           const float inv[3], float tmax, float& t0,
+                                           float& t1) {
+  const float3 e = node_ext(nd.meta);
+  const float ext[3] = {e.x, e.y, e.z};
+  t0 = 0.0f;
+  t1 = tmax;
+  bool hit = true;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float lo = nd.lo[c], hi = lo + ext[c];
+    if (n[c] == 0.0f) {
+      hit &= (lo <= xv[c]) && (xv[c] < hi);
+    } else {
+      const float ta = (lo - xv[c]) * inv[c], tb = (hi - xv[c]) * inv[c];
+      t0 = fmaxf(t0, fminf(ta, tb));
+      t1 = fminf(t1, fmaxf(ta, tb));
+    }
+  }
+  return hit && (t0 < t1);
+}
+
 // The halves of an opened node that a beam (x + t n, t in [t0, t1), the
 // node's own chord) crosses and that hold some absorption, which half the
 // beam meets first (the receiver's side), and each half's chord [lt0, lt1),
@@ -424,9 +448,9 @@ int read_status(Tree* t, cudaStream_t st);
 
 // Per-warp shared memory of a walk block: the traversal stacks, the beam
 // bucket offsets, the beam order and its 32 bucket counts, the next-beam
-// counter.
-inline size_t walk_smem(int warps, int stack_ints, int npix) {
-  return size_t(warps) * (stack_ints + 2 * npix + 34) * sizeof(int);
+// counter (padded to 16 bytes), the receiver's ancestor records.
+inline size_t walk_smem(int warps, int stack_ints, int npix, int max_depth) {
+  return size_t(warps) * (stack_ints + 2 * npix + 36 + 8 * (max_depth + 1)) * sizeof(int);
 }
 
 }  // namespace trevr2
