@@ -164,23 +164,9 @@ __device__ __forceinline__ void walk_receiver_si(const WalkArgs& a, int si, floa
   const float4 xr = a.pos32[si];
   // the receiver in FP32, on the FP64 side of every box face
   const float3 x = grazing_coords(a, si, make_float3(xr.x, xr.y, xr.z));
-  // the receiver's ancestors, root first, by the same half-open decisions
+  // the receiver's ancestors, root first
   NodeW* chain = reinterpret_cast<NodeW*>(off + 2 * a.npix + 36);
-  int leaf = 0;
-  {
-    const float xv[3] = {x.x, x.y, x.z};
-    for (int d = 0;; ++d) {
-      const NodeW nd = a.nodes[leaf];
-      if (lane == 0) chain[d] = nd;
-      if (nd.meta & kMetaLeaf) break;
-      bool lower_first, lh, uh;
-      float l0, l1, u0, u1;
-      const float zero3[3] = {0.0f, 0.0f, 0.0f};
-      crossed_halves(nd, xv, zero3, zero3, 0.0f, 1.0f, lower_first, lh, uh, l0, l1, u0, u1);
-      leaf = lower_first ? nd.child : nd.child + 1;
-    }
-    __syncwarp();
-  }
+  const int leaf = build_chain(a.nodes, x, lane, chain);
   float Js[NBP], Jc[NBP];
 #pragma unroll
   for (int b = 0; b < NBP; ++b) Js[b] = Jc[b] = 0.0f;

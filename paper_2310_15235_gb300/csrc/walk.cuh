@@ -133,6 +133,27 @@ __device__ __forceinline__ void crossed_halves(const NodeW& nd, const float xv[3
   upper_hit &= (nd.meta & kMetaChild1Alpha) != 0;
 }
 
+// The receiver's ancestors, root first, into chain[] (shared memory, written
+// by lane 0) by the same half-open decisions as the beams' near halves;
+// returns the receiver's leaf.
+__device__ __forceinline__ int build_chain(const NodeW* __restrict__ nodes, float3 x, int lane,
+                                           NodeW* chain) {
+  const float xv[3] = {x.x, x.y, x.z};
+  const float zero3[3] = {0.0f, 0.0f, 0.0f};
+  int leaf = 0;
+  for (int d = 0;; ++d) {
+    const NodeW nd = nodes[leaf];
+    if (lane == 0) chain[d] = nd;
+    if (nd.meta & kMetaLeaf) break;
+    bool lower_first, lh, uh;
+    float l0, l1, u0, u1;
+    crossed_halves(nd, xv, zero3, zero3, 0.0f, 1.0f, lower_first, lh, uh, l0, l1, u0, u1);
+    leaf = lower_first ? nd.child : nd.child + 1;
+  }
+  __syncwarp();
+  return leaf;
+}
+
 // FP64 opening decision, the definition evaluated without contraction.
 static __device__ __noinline__ bool opens64(const double* __restrict__ x64, double B,
                                             double theta, float lx, float ly, float lz,
