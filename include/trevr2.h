@@ -129,7 +129,7 @@ int trevr2_prepare(trevr2_tree* tree, int nside, void* stream);
  *    earlier trevr2_J with the same nside); otherwise EINVAL;
  *  - the walk buffers live in one fixed 16 MiB device array inside the
  *    library (256 source records per warp and pass, which caps the grid at
- *    1,260 resident warps).  The walk loops over receivers and makes more
+ *    1,820 resident warps).  The walk loops over receivers and makes more
  *    passes when a receiver has more sources, so any A works; a launch that
  *    would need more than the array holds is rejected with EUNSUPPORTED.
  * Every process that loads the library holds that array on each GPU it uses

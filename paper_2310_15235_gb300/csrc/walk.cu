@@ -449,17 +449,18 @@ int config_walk_kernel(const void* fn, int warps, size_t smem, int* per_sm, int*
   return TREVR2_OK;
 }
 
-// Walk buffers: per warp, M source records in and out and their beams.
+// Walk buffers: per warp, M source records in and out and their beams; the
+// optical depths of the binned records reuse the space of the unbinned ones.
 static size_t walk_buffer_bytes(size_t warps, int M) {
-  return warps * size_t(M) * (2 * sizeof(SrcEntry) + 4 * sizeof(float) + sizeof(int));
+  return warps * size_t(M) * (2 * sizeof(SrcEntry) + sizeof(int));
 }
 
 static void place_walk_buffers(char* base, size_t warps, int M, SrcEntry** U, SrcEntry** V,
                                float** T, int** Up) {
   *U = reinterpret_cast<SrcEntry*>(base);
   *V = reinterpret_cast<SrcEntry*>(base + warps * M * sizeof(SrcEntry));
-  *T = reinterpret_cast<float*>(base + 2 * warps * M * sizeof(SrcEntry));
-  *Up = reinterpret_cast<int*>(base + 2 * warps * M * sizeof(SrcEntry) + warps * M * 4 * sizeof(float));
+  *T = reinterpret_cast<float*>(*U);  // the staged records are dead once binned
+  *Up = reinterpret_cast<int*>(base + 2 * warps * M * sizeof(SrcEntry));
 }
 
 __global__ void k_order_keys(const int64_t* __restrict__ active, int64_t A, int64_t N,
