@@ -352,7 +352,7 @@ static __device__ int phase_sources(const WalkArgs& a, float3 x, int si, int lan
 
 // Bucket the n sources of U by beam into V; off[k] ends as the end of
 // bucket k (its start is off[k-1], or 0).  Each bucket is sorted by s.
-static __device__ void bin_sources(const WalkArgs& a, int lane, const SrcEntry* U, const int* Up, int n,
+static __device__ void bin_sources(const WalkArgs& a, int lane, SrcEntry* U, const int* Up, int n,
                             SrcEntry* V, int* off) {
   const int npix = a.npix;
   for (int k = lane; k < npix; k += 32) off[k] = 0;
@@ -377,19 +377,25 @@ static __device__ void bin_sources(const WalkArgs& a, int lane, const SrcEntry* 
     V[slot] = U[e];
   }
   __syncwarp();
-  // insertion sort of each bucket by projected distance
-  for (int k = lane; k < npix; k += 32) {
-    const int s0 = k ? off[k - 1] : 0, s1 = off[k];
-    for (int i = s0 + 1; i < s1; ++i) {
-      const SrcEntry v = V[i];
-      int j = i - 1;
-      while (j >= s0 && V[j].s > v.s) {
-        V[j + 1] = V[j];
-        --j;
-      }
-      V[j + 1] = v;
+  // each record's rank in its bucket by (projected distance, source), all
+  // lanes at once: the sorted buckets go to U, then back to V
+  for (int e = lane; e < n; e += 32) {
+    int lo = 0, hi = npix - 1;  // the bucket holding position e: first k with off[k] > e
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (off[mid] > e) hi = mid; else lo = mid + 1;
     }
+    const int s0 = lo ? off[lo - 1] : 0, s1 = off[lo];
+    const SrcEntry v = V[e];
+    int r = 0;
+    for (int j = s0; j < s1; ++j) {
+      const SrcEntry w = V[j];
+      r += (w.s < v.s) || (w.s == v.s && w.ref < v.ref);
+    }
+    U[s0 + r] = v;
   }
+  __syncwarp();
+  for (int e = lane; e < n; e += 32) V[e] = U[e];
   __syncwarp();
 }
 
