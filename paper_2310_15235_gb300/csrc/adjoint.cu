@@ -443,9 +443,10 @@ __device__ __forceinline__ void adjoint_receiver(const AdjArgs& g, int64_t slot,
   for (int b = 0; b < NBP; ++b) Js[b] = Jc[b] = 0.0f;
   for (int lo = 0;; lo += a.M) {
     const int total = phase_sources(a, x, si, lane, stk, a.stack_ints, U, Up, lo);
-    const int n = min(total - lo, a.M);
+    const int staged = min(total - lo, a.M);
+    make_sources(a, x, si, lane, U, Up, staged);
+    const int n = staged > 0 ? bin_sources(a, lane, U, Up, staged, V, off) : 0;
     if (n > 0) {
-      bin_sources(a, lane, U, Up, n, V, off);
       // bin_sources leaves the beams in Up unsorted: put them in V's order
       for (int e = lane; e < a.npix; e += 32) {
         const int s0 = e ? off[e - 1] : 0, s1 = off[e];

@@ -172,9 +172,10 @@ __device__ __forceinline__ void walk_receiver_si(const WalkArgs& a, int si, floa
   for (int b = 0; b < NBP; ++b) Js[b] = Jc[b] = 0.0f;
   for (int lo = 0;; lo += a.M) {
     const int total = phase_sources(a, x, si, lane, stk, a.stack_ints, U, Up, lo);
-    const int n = min(total - lo, a.M);
+    const int staged = min(total - lo, a.M);
+    make_sources(a, x, si, lane, U, Up, staged);
+    const int n = staged > 0 ? bin_sources(a, lane, U, Up, staged, V, off) : 0;
     if (n > 0) {
-      bin_sources(a, lane, U, Up, n, V, off);
       int* order = off + a.npix;
       const int nbeams = order_beams(a, lane, V, off, order, order + a.npix);
       if (lane == 0) *next_beam = 32;

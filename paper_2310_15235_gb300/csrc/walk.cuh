@@ -267,8 +267,10 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
   return v;
 }
 
-// Phase S for the sources whose running index is in [lo, lo + M).  Returns
-// the total number of sources of this receiver (warp-uniform).
+// Phase S for the sources whose running index is in [lo, lo + M): their
+// references (a cell index, or an element index with kRefElement) go to
+// U[].ref; make_sources then fills the records.  Returns the total number of
+// sources of this receiver (warp-uniform).
 static __device__ int phase_sources(const WalkArgs& a, float3 x, int si, int lane, int* stk, int cap,
                              SrcEntry* U, int* Up, int lo) {
   int sp = 1;
@@ -283,15 +285,11 @@ static __device__ int phase_sources(const WalkArgs& a, float3 x, int si, int lan
     __syncwarp();
     int npush = 0, child = -1, leaf_first = 0, leaf_count = 0;
     bool emit_node = false;
-    SrcEntry ent;
-    int pix = 0;
     if (q >= 0) {
       const NodeW nd = a.nodes[q];
       if (nd.meta & kMetaHasL) {
         if (!cell_opens(a, q, nd, x, si)) {
-          const float4 c = a.csrc[q];
-          emit_node = make_source(a, make_float3(c.x, c.y, c.z), a.c64 + 3 * int64_t(q), x, si, q,
-                                  ent, pix);
+          emit_node = true;
         } else if (nd.meta & kMetaLeaf) {
           leaf_first = nd.aux;
           leaf_count = nd.count;
@@ -318,10 +316,7 @@ static __device__ int phase_sources(const WalkArgs& a, float3 x, int si, int lan
     {
       const unsigned m = __ballot_sync(0xffffffffu, emit_node);
       const int idx = emitted + __popc(m & lt) - lo;
-      if (emit_node && idx >= 0 && idx < a.M) {
-        U[idx] = ent;
-        Up[idx] = pix;
-      }
+      if (emit_node && idx >= 0 && idx < a.M) U[idx].ref = q;
       emitted += __popc(m);
     }
     // luminous elements of opened leaves
@@ -330,19 +325,11 @@ static __device__ int phase_sources(const WalkArgs& a, float3 x, int si, int lan
     for (int o = 16; o > 0; o >>= 1) maxc = max(maxc, __shfl_xor_sync(0xffffffffu, maxc, o));
     for (int e = 0; e < maxc; ++e) {
       bool em = false;
-      if (e < leaf_count) {
-        const int sj = leaf_first + e;
-        const float4 pj = a.pos32[sj];
-        if (pj.w > 0.0f && sj != si)
-          em = make_source(a, make_float3(pj.x, pj.y, pj.z), a.pos64 + 3 * int64_t(sj), x, si,
-                           sj | kRefElement, ent, pix);
-      }
+      const int sj = leaf_first + e;
+      if (e < leaf_count) em = a.pos32[sj].w > 0.0f && sj != si;
       const unsigned m = __ballot_sync(0xffffffffu, em);
       const int idx = emitted + __popc(m & lt) - lo;
-      if (em && idx >= 0 && idx < a.M) {
-        U[idx] = ent;
-        Up[idx] = pix;
-      }
+      if (em && idx >= 0 && idx < a.M) U[idx].ref = sj | kRefElement;
       emitted += __popc(m);
     }
     __syncwarp();
@@ -350,14 +337,43 @@ static __device__ int phase_sources(const WalkArgs& a, float3 x, int si, int lan
   return emitted;
 }
 
-// Bucket the n sources of U by beam into V; off[k] ends as the end of
-// bucket k (its start is off[k-1], or 0).  Each bucket is sorted by s.
-static __device__ void bin_sources(const WalkArgs& a, int lane, SrcEntry* U, const int* Up, int n,
-                            SrcEntry* V, int* off) {
+// The records of the n staged sources, all lanes at once: beam, projected
+// distance, r/s, kernel (make_source); a source the method skips (r = 0, or
+// not in front of its beam) gets beam -1.
+static __device__ void make_sources(const WalkArgs& a, float3 x, int si, int lane, SrcEntry* U,
+                                    int* Up, int n) {
+  for (int e = lane; e < n; e += 32) {
+    const int ref = U[e].ref;
+    float3 p;
+    const double* p64;
+    if (ref & kRefElement) {
+      const int64_t j = ref & 0x7fffffff;
+      const float4 pj = a.pos32[j];
+      p = make_float3(pj.x, pj.y, pj.z);
+      p64 = a.pos64 + 3 * j;
+    } else {
+      const float4 c = a.csrc[ref];
+      p = make_float3(c.x, c.y, c.z);
+      p64 = a.c64 + 3 * int64_t(ref);
+    }
+    SrcEntry ent;
+    int pix = -1;
+    if (make_source(a, p, p64, x, si, ref, ent, pix)) U[e] = ent; else pix = -1;
+    Up[e] = pix;
+  }
+  __syncwarp();
+}
+
+// Bucket the n records of U by beam into V, skipping beam -1; off[k] ends as
+// the end of bucket k (its start is off[k-1], or 0).  Each bucket is sorted
+// by (s, source).  Returns the number of records binned.
+static __device__ int bin_sources(const WalkArgs& a, int lane, SrcEntry* U, const int* Up, int n,
+                                  SrcEntry* V, int* off) {
   const int npix = a.npix;
   for (int k = lane; k < npix; k += 32) off[k] = 0;
   __syncwarp();
-  for (int e = lane; e < n; e += 32) atomicAdd(&off[Up[e]], 1);
+  for (int e = lane; e < n; e += 32)
+    if (Up[e] >= 0) atomicAdd(&off[Up[e]], 1);
   __syncwarp();
   // exclusive scan of the bucket sizes
   const int per = (npix + 31) / 32;
@@ -373,10 +389,12 @@ static __device__ void bin_sources(const WalkArgs& a, int lane, SrcEntry* U, con
   }
   __syncwarp();
   for (int e = lane; e < n; e += 32) {
+    if (Up[e] < 0) continue;
     const int slot = atomicAdd(&off[Up[e]], 1);
     V[slot] = U[e];
   }
   __syncwarp();
+  n = off[npix - 1];  // records binned
   // each record's rank in its bucket by (projected distance, source), all
   // lanes at once: the sorted buckets go to U, then back to V
   for (int e = lane; e < n; e += 32) {
@@ -397,6 +415,7 @@ static __device__ void bin_sources(const WalkArgs& a, int lane, SrcEntry* U, con
   __syncwarp();
   for (int e = lane; e < n; e += 32) V[e] = U[e];
   __syncwarp();
+  return n;
 }
 
 template <int NBP>
