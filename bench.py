@@ -37,7 +37,7 @@ NODE_BYTES = 32  # walk record of one node
 # capture of the 96^3 version of the benchmark field (2.30 GB read + 8.71 GB
 # written for 884,736 receivers); scaled by the receivers of a launch.  It
 # must be measured again (or set to None) whenever the walk kernel changes.
-WALK_TRAFFIC_BYTES_PER_RECEIVER = 12436.0
+WALK_TRAFFIC_BYTES_PER_RECEIVER = None
 
 
 def _workload_name(case):
