@@ -34,10 +34,10 @@ METRIC = "active receiver x HEALPix-ray x band / s"
 UNIT = "receiver*ray*band/s"
 NODE_BYTES = 32  # walk record of one node
 # DRAM bytes (read + write) per receiver of one k_walk launch, from the ncu
-# capture of the 96^3 version of the benchmark field (2.30 GB read + 8.71 GB
+# capture of the 96^3 version of the benchmark field (2.42 GB read + 8.12 GB
 # written for 884,736 receivers); scaled by the receivers of a launch.  It
 # must be measured again (or set to None) whenever the walk kernel changes.
-WALK_TRAFFIC_BYTES_PER_RECEIVER = None
+WALK_TRAFFIC_BYTES_PER_RECEIVER = 11915.0
 
 
 def _workload_name(case):
