@@ -31,6 +31,7 @@ _lib = None
 
 FLAG_SOFT = 1
 FLAG_THICK = 2
+FLAG_LINEAR = 8
 
 
 def build(force: bool = False) -> str:
@@ -64,7 +65,7 @@ def _load():
         lib.oracle_tree_export.argtypes = [P] + [P] * 9
         lib.oracle_tree_aggregates.argtypes = [P, P, P, P, P, P]
         lib.oracle_alpha_table.restype = i32
-        lib.oracle_alpha_table.argtypes = [P, i32, P]
+        lib.oracle_alpha_table.argtypes = [P, i32, i32, P]
         lib.oracle_pix2vec.argtypes = [i32, P]
         lib.oracle_vec2pix.argtypes = [i32, P, i64, P]
         lib.oracle_pair_of_pixel.restype = i64
@@ -216,9 +217,9 @@ class OracleTree:
                                        _p(o["B"]), _p(o["alpha_leaf"]))
         return o
 
-    def alpha_table(self, nside: int) -> np.ndarray:
+    def alpha_table(self, nside: int, linear: bool = False) -> np.ndarray:
         out = np.empty((self.num_nodes, 6 * nside * nside, self.nb))
-        if _load().oracle_alpha_table(self._h, int(nside), _p(out)) != 0:
+        if _load().oracle_alpha_table(self._h, int(nside), int(bool(linear)), _p(out)) != 0:
             raise ValueError("bad nside")
         return out
 

@@ -40,6 +40,9 @@
 //     far-field kernel is L/(4 pi r^2).
 //  R7 Finite-size kernel radius (3/(4 pi))^(1/2) h = 0.48860 h.
 //  R8 Graze tie-break: boxes are half-open [lo, hi) on each axis.
+//  R9 FLAG_LINEAR replaces Eq. transmissionavg by the volume-weighted linear
+//     average of the two halves' absorption, the scheme Sec. 2.6 compares
+//     it with; it is direction independent (the same value in every pair).
 
 #include <algorithm>
 #include <atomic>
@@ -470,10 +473,12 @@ Aggregates<T> compute_aggregates(const Tree& t, const std::vector<T>& kappa,
 }
 
 // Per-direction-pair alpha for every node: leaves repeat their isotropic
-// alpha; internal nodes combine their two halves by Eq. transmissionavg,
-// deepest nodes first so children are done before parents.
+// alpha; internal nodes combine their two halves by Eq. transmissionavg, or
+// (linear) by the volume-weighted linear average of the halves' absorption
+// that Sec. 2.6 compares it with, deepest nodes first so children are done
+// before parents.
 template <class T>
-std::vector<T> alpha_tables(const Tree& t, const Aggregates<T>& ag, int nside) {
+std::vector<T> alpha_tables(const Tree& t, const Aggregates<T>& ag, int nside, bool linear) {
   const int64_t n = static_cast<int64_t>(t.nodes.size());
   const int nb = t.nb;
   const int64_t P = 6 * static_cast<int64_t>(nside) * nside;
@@ -492,6 +497,20 @@ std::vector<T> alpha_tables(const Tree& t, const Aggregates<T>& ag, int nside) {
     double E[3] = {bhi[0] - blo[0], bhi[1] - blo[1], bhi[2] - blo[2]};
     int axis = nd.depth % 3;
     int64_t c1 = nd.child, c2 = nd.child + 1;
+    if (linear) {
+      // alpha = (V_1 alpha_1 + V_2 alpha_2) / V over the two halves' boxes
+      double lo1[3], hi1[3], lo2[3], hi2[3];
+      node_box(t.nodes[c1], t.lo, t.size, lo1, hi1);
+      node_box(t.nodes[c2], t.lo, t.size, lo2, hi2);
+      const double V = E[0] * E[1] * E[2];
+      const double V1 = (hi1[0] - lo1[0]) * (hi1[1] - lo1[1]) * (hi1[2] - lo1[2]);
+      const double V2 = (hi2[0] - lo2[0]) * (hi2[1] - lo2[1]) * (hi2[2] - lo2[2]);
+      for (int64_t p = 0; p < P; ++p)
+        for (int b = 0; b < nb; ++b)
+          tab[(q * P + p) * nb + b] =
+              (V1 * tab[(c1 * P + p) * nb + b] + V2 * tab[(c2 * P + p) * nb + b]) / V;
+      continue;
+    }
     for (int64_t p = 0; p < P; ++p) {
       TransGeo g = transmission_geometry(E, axis, &dirs[3 * p]);
       for (int b = 0; b < nb; ++b) {
@@ -523,7 +542,7 @@ bool ray_chord(const double x[3], const double n[3], const double blo[3], const 
   return t1 > t0;
 }
 
-enum : uint32_t { FLAG_SOFT = 1u, FLAG_THICK = 2u };
+enum : uint32_t { FLAG_SOFT = 1u, FLAG_THICK = 2u, FLAG_LINEAR = 8u };
 
 struct WalkStats {
   int64_t visited = 0;   // nodes given the opening test
@@ -718,12 +737,14 @@ struct OracleTree {
   Aggregates<double> ag;
   std::vector<double> tab;
   int tab_nside = -1;
+  bool tab_linear = false;
 };
 
-void ensure_table(OracleTree& ot, int nside) {
-  if (ot.tab_nside == nside) return;
-  ot.tab = alpha_tables(ot.t, ot.ag, nside);
+void ensure_table(OracleTree& ot, int nside, bool linear = false) {
+  if (ot.tab_nside == nside && ot.tab_linear == linear) return;
+  ot.tab = alpha_tables(ot.t, ot.ag, nside, linear);
   ot.tab_nside = nside;
+  ot.tab_linear = linear;
 }
 
 bool valid_nside(int nside) { return nside >= 1 && nside <= 64 && (nside & (nside - 1)) == 0; }
@@ -832,10 +853,10 @@ void oracle_tree_aggregates(void* h, double* L, double* Ltot, double* c, double*
 }
 
 // out: [n_nodes][6 nside^2][nb]
-int oracle_alpha_table(void* h, int nside, double* out) {
+int oracle_alpha_table(void* h, int nside, int linear, double* out) {
   if (!valid_nside(nside)) return -1;
   OracleTree& ot = *static_cast<OracleTree*>(h);
-  ensure_table(ot, nside);
+  ensure_table(ot, nside, linear != 0);
   std::memcpy(out, ot.tab.data(), ot.tab.size() * sizeof(double));
   return 0;
 }
@@ -877,7 +898,7 @@ int oracle_J(void* h, const int64_t* active, int64_t A, int nside, double theta,
   OracleTree& ot = *static_cast<OracleTree*>(h);
   for (int64_t a = 0; a < A; ++a)
     if (active[a] < 0 || active[a] >= ot.t.N) return -1;
-  ensure_table(ot, nside);
+  ensure_table(ot, nside, (flags & FLAG_LINEAR) != 0);
   Problem<double> pr = make_problem<double>(ot.t, ot.ag, ot.tab, ot.t.kappa, ot.t.lum, nside,
                                             theta, flags);
   const int nb = ot.t.nb;
@@ -909,7 +930,7 @@ int oracle_J_deriv(void* h, const int64_t* active, int64_t A, int nside, double 
   if (which == 0) kappa[elem * nb + band].d = 1.0;
   else lum[elem * nb + band].d = 1.0;
   Aggregates<Dual> ag = compute_aggregates<Dual>(t, kappa, lum);
-  std::vector<Dual> tab = alpha_tables<Dual>(t, ag, nside);
+  std::vector<Dual> tab = alpha_tables<Dual>(t, ag, nside, (flags & FLAG_LINEAR) != 0);
   Problem<Dual> pr = make_problem<Dual>(t, ag, tab, kappa, lum, nside, theta, flags);
   parallel_for(A, nthreads, [&](int64_t a) {
     std::vector<Dual> Jd(nb);

@@ -598,3 +598,55 @@ def test_dual_loss_gradient_matches_central_difference_64(oracle_mod, flags):
     scale = np.abs(fd).max()
     assert scale > 0
     np.testing.assert_allclose(dual, fd, rtol=1e-5, atol=1e-7 * scale)
+
+
+# ----------------------------------------------------------------------------
+# Linear absorption averaging (the comparison scheme of Sec. 2.6, flag LINEAR)
+
+def test_linear_average_is_column_over_volume(oracle_mod):
+    """With linear averaging every cell's alpha, in every direction, is the
+    volume-weighted mean of its leaves' bucket alpha, i.e. the cell's total
+    kappa m over its volume, computed here directly from the elements."""
+    case = workloads.random_case(400, 20, nb=2, seed=71, clumped=True)
+    t = oracle_mod.OracleTree.from_case(case)
+    e = t.export()
+    tab = t.alpha_table(2, linear=True)
+    kap, m = case["kappa"].astype(np.float64), case["mass"].astype(np.float64)
+    for q in range(len(e["depth"])):
+        idx = e["perm"][e["first"][q]: e["first"][q] + e["count"][q]]
+        V = np.prod(e["box"][q, 3:] - e["box"][q, :3])
+        want = (kap[idx] * m[idx, None]).sum(0) / V
+        np.testing.assert_allclose(tab[q], np.broadcast_to(want, tab[q].shape), rtol=1e-12,
+                                   atol=1e-12 * max(want.max(), 1e-300))
+
+
+@pytest.mark.parametrize("nside,theta", [(2, 0.75), (4, 0.5)])
+def test_linear_closed_form_one_source(oracle_mod, nside, theta):
+    """In a uniform medium both averages keep alpha = kappa rho, so the linear
+    flag gives the closed form L e^{-kappa rho r} / (4 pi r^2) as well."""
+    case = workloads.uniform_point_source(offset=True)
+    t = oracle_mod.OracleTree.from_case(case)
+    J = t.J(case["active"], nside, theta, flags=oracle_mod.FLAG_LINEAR)
+    src = case["pos"][-1]
+    ok = _inside_mask(case, nside, oracle_mod, [src])
+    r = np.linalg.norm(case["pos"][case["active"]] - src, axis=1)
+    np.testing.assert_allclose(J[ok, 0], np.exp(-2.0 * r)[ok] / (4 * np.pi * r[ok] ** 2),
+                               rtol=1e-12)
+
+
+def test_linear_average_never_lets_more_through(oracle_mod):
+    """The transmission average of a pair never exceeds the linear one (the
+    exponential is convex and the transmission weights have the linear mean
+    as their exponent's mean), so at every cell and direction alpha_lin >=
+    alpha_trans, and every receiver gets J_lin <= J_trans; in a clumpy field
+    the two differ (Sec. 2.6: linear averaging overestimates the opacity)."""
+    case = workloads.random_case(900, 30, nb=2, seed=72, clumped=True, kappa_scale=60.0,
+                                 n_active=150)
+    t = oracle_mod.OracleTree.from_case(case)
+    lin, tr = t.alpha_table(2, linear=True), t.alpha_table(2)
+    assert np.all(lin >= tr * (1 - 1e-12) - 1e-300)
+    Jl = t.J(case["active"], 2, 0.75, flags=oracle_mod.FLAG_LINEAR)
+    Jt = t.J(case["active"], 2, 0.75)
+    assert np.all(Jl <= Jt * (1 + 1e-12))
+    assert ((Jt - Jl) / Jt).max() > 1e-2  # accepted internal cells differ
+    assert (lin > tr * 1.01).any()
