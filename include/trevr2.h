@@ -49,6 +49,9 @@ extern "C" {
 #define TREVR2_SOFT 1u   /* finite-size element kernel, Eq. intint (Sec. 2.2)   */
 #define TREVR2_THICK 2u  /* optically thick element factor, Eq. taucorr (Sec. 2.1) */
 #define TREVR2_ASYNC 4u  /* do not synchronise; check later with trevr2_status */
+#define TREVR2_LINEAR 8u /* internal cells take the volume-weighted linear average of
+                            their halves' absorption, the scheme Sec. 2.6 compares
+                            Eq. transmissionavg with (direction independent) */
 
 /* Supported sizes: 1 <= nb <= 4 bands; nside a power of two in [1, 16];
  * N < 2^31 elements; 1 <= bucket <= 4096. */
@@ -94,10 +97,11 @@ int trevr2_build(const double* pos, const float* mass, const float* kappa, const
  *
  *  active  [A] int64  receiver indices in the caller's element order
  *  nside   HEALPix resolution (power of two, 1..TREVR2_MAX_NSIDE); the alpha
- *          tables for a new nside are built on first use and cached
+ *          tables for a new nside (and averaging) are built on first use
+ *          and cached
  *  theta   opening parameter theta_rad > 0 (paper default 0.75)
  *  bands   host [nbsel] band indices to return, or NULL = all nb bands
- *  flags   TREVR2_SOFT | TREVR2_THICK | TREVR2_ASYNC
+ *  flags   TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_ASYNC
  *  J       [A][nbsel] float32 output, overwritten
  * Active indices outside [0, N) give EINVAL (their rows are set to NaN).
  * Without TREVR2_ASYNC the call synchronises `stream` and returns any device
@@ -112,7 +116,8 @@ int trevr2_J(trevr2_tree* tree, const int64_t* active, int64_t A, int nside, flo
  * Eq. transmissionavg (Sec. 2.6; N_ray/2 values per cell and band) and the
  * HEALPix beam table for `nside`, without running a walk.  trevr2_J does the
  * same on first use of an nside; calling this first keeps that work out of
- * a later trevr2_J.  Stream ordered, does not synchronise.
+ * a later trevr2_J.  The linear-average tables (TREVR2_LINEAR) are built by
+ * the first call that asks for them.  Stream ordered, does not synchronise.
  * Errors: EINVAL (NULL tree, bad nside), ENOMEM, ECUDA.
  */
 int trevr2_prepare(trevr2_tree* tree, int nside, void* stream);
@@ -126,7 +131,8 @@ int trevr2_prepare(trevr2_tree* tree, int nside, void* stream);
  *
  * Arguments, output and errors are those of trevr2_J, with two differences:
  *  - the tables for `nside` must already exist (trevr2_prepare, or an
- *    earlier trevr2_J with the same nside); otherwise EINVAL;
+ *    earlier trevr2_J with the same nside; with TREVR2_LINEAR an earlier
+ *    trevr2_J with that flag); otherwise EINVAL;
  *  - the walk buffers live in one fixed 16 MiB device array inside the
  *    library (256 source records per warp and pass, which caps the grid at
  *    1,820 resident warps).  The walk loops over receivers and makes more

@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(WARPS * 32, kAdjBlocksPerSM) k_walk_adjoint(co
 
 // Step 2: one depth of the tables' adjoint, parents before children.
 template <int NBP>
-__global__ void k_alpha_adjoint_level(int64_t lb, int64_t le, int P, int nb,
+__global__ void k_alpha_adjoint_level(int64_t lb, int64_t le, int P, int nb, bool linear,
                                       const NodeW* __restrict__ nodes,
                                       const int* __restrict__ int_index,
                                       const float* __restrict__ alpha_leaf,
@@ -559,8 +559,9 @@ __global__ void k_alpha_adjoint_level(int64_t lb, int64_t le, int P, int nb,
     const float e2 = gg.w1 > 0.0f ? gg.w1 * expf(-(x2 - m)) : 0.0f;
     const float e12 = gg.w12 > 0.0f ? gg.w12 * expf(-(x12 - m)) : 0.0f;
     const float iS = 1.0f / (e1 + e2 + e12);
-    const float d1 = G.v[b] * (e1 + 0.5f * e12) * iS;
-    const float d2 = G.v[b] * (e2 + 0.5f * e12) * iS;
+    // linear average: dalpha/dalpha_1 = dalpha/dalpha_2 = 1/2
+    const float d1 = linear ? 0.5f * G.v[b] : G.v[b] * (e1 + 0.5f * e12) * iS;
+    const float d2 = linear ? 0.5f * G.v[b] : G.v[b] * (e2 + 0.5f * e12) * iS;
     if (i1 < 0) atomicAdd(g_aleaf + int64_t(c) * NBP + b, d1);
     else g_atab[(int64_t(i1) * P + p) * NBP + b] += d1;
     if (i2 < 0) atomicAdd(g_aleaf + int64_t(c + 1) * NBP + b, d2);
@@ -655,7 +656,7 @@ extern "C" int trevr2_J_backward(trevr2_tree* tree, const int64_t* active, int64
     set_error("trevr2_J_backward: theta must be positive and finite");
     return TREVR2_EINVAL;
   }
-  if (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_ASYNC)) {
+  if (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_ASYNC)) {
     set_error("trevr2_J_backward: unknown flags 0x%x", flags);
     return TREVR2_EINVAL;
   }
@@ -679,7 +680,8 @@ extern "C" int trevr2_J_backward(trevr2_tree* tree, const int64_t* active, int64
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   t->last_stream = st;
   Table* tb = nullptr;
-  T2_CHECK(ensure_table(t, nside, st, &tb));
+  const bool linear = (flags & TREVR2_LINEAR) != 0;
+  T2_CHECK(ensure_table(t, nside, st, &tb, linear));
   const int P = 6 * nside * nside;
   const int nbp = t->nbp;
   const int64_t n = t->n_nodes;
@@ -753,9 +755,9 @@ extern "C" int trevr2_J_backward(trevr2_tree* tree, const int64_t* active, int64
       if (work == 0) continue;
       const unsigned nblk = unsigned((work + 255) / 256);
       switch (nbp) {
-        case 1: k_alpha_adjoint_level<1><<<nblk, 256, 0, st>>>(lb, le, P, t->nb, t->nodes, t->int_index, t->alpha_leaf, tb->geo, tb->alpha, g.g_atab, g.g_aleaf); break;
-        case 2: k_alpha_adjoint_level<2><<<nblk, 256, 0, st>>>(lb, le, P, t->nb, t->nodes, t->int_index, t->alpha_leaf, tb->geo, tb->alpha, g.g_atab, g.g_aleaf); break;
-        default: k_alpha_adjoint_level<4><<<nblk, 256, 0, st>>>(lb, le, P, t->nb, t->nodes, t->int_index, t->alpha_leaf, tb->geo, tb->alpha, g.g_atab, g.g_aleaf); break;
+        case 1: k_alpha_adjoint_level<1><<<nblk, 256, 0, st>>>(lb, le, P, t->nb, linear, t->nodes, t->int_index, t->alpha_leaf, tb->geo, tb->alpha, g.g_atab, g.g_aleaf); break;
+        case 2: k_alpha_adjoint_level<2><<<nblk, 256, 0, st>>>(lb, le, P, t->nb, linear, t->nodes, t->int_index, t->alpha_leaf, tb->geo, tb->alpha, g.g_atab, g.g_aleaf); break;
+        default: k_alpha_adjoint_level<4><<<nblk, 256, 0, st>>>(lb, le, P, t->nb, linear, t->nodes, t->int_index, t->alpha_leaf, tb->geo, tb->alpha, g.g_atab, g.g_aleaf); break;
       }
       note_launch();
     }

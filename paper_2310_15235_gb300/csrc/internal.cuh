@@ -65,6 +65,7 @@ struct __align__(16) TransGeo {
 
 struct Table {
   int nside = 0;
+  bool linear = false;         // linear absorption average instead of Eq. transmissionavg
   float* alpha = nullptr;      // [n_internal][P][nbp] normalised absorption
   float4* dirs = nullptr;      // [npix] beam directions (xyz), w = pair index (int bits)
   double* dirs64 = nullptr;    // [npix][3]
@@ -173,8 +174,10 @@ size_t radix_ws_bytes(int64_t n);
 int radix_sort_u64_i32(uint64_t* keys, int* vals, int64_t n, cudaStream_t st, int key_bits = 64,
                        void* ws = nullptr);
 
-// Alpha tables and beam directions for one nside (built and cached).
-int ensure_table(Tree* t, int nside, cudaStream_t st, Table** out);
+// Alpha tables and beam directions for one nside and averaging (built and
+// cached): Eq. transmissionavg, or with `linear` the volume-weighted linear
+// average of the halves (Sec. 2.6's comparison scheme).
+int ensure_table(Tree* t, int nside, cudaStream_t st, Table** out, bool linear = false);
 
 inline int nbp_of(int nb) { return nb <= 1 ? 1 : (nb == 2 ? 2 : 4); }
 

@@ -10,7 +10,10 @@
 // centre of the shared face (the cell centre).  The through-ray term is the
 // product of the two half-cell transmissions: the printed sum of the two
 // exponentials exceeds 1 for a transparent cell and contradicts the paper's
-// own worked example.  Leaves are isotropic (bucket absorption).
+// own worked example.  Leaves are isotropic (bucket absorption).  With
+// TREVR2_LINEAR the halves are combined by their volume-weighted linear
+// average instead (Sec. 2.6's comparison scheme): (alpha_1 + alpha_2) / 2,
+// the same in every direction pair.
 //
 // Cell shapes repeat every three levels (cube split on x; 1:2:2 split on y;
 // 1:1:2 split on z), so the weights depend only on (depth mod 3, beam pair)
@@ -99,7 +102,8 @@ __device__ __forceinline__ float combine_alpha(float a1, float a2, float w1, flo
 }
 
 template <int NBP>
-__global__ void k_alpha_level(int64_t lb, int64_t le, int P, int nb, const NodeW* __restrict__ nodes,
+__global__ void k_alpha_level(int64_t lb, int64_t le, int P, int nb, bool linear,
+                              const NodeW* __restrict__ nodes,
                               const int* __restrict__ int_index,
                               const float* __restrict__ alpha_leaf,
                               const TransGeo* __restrict__ geo, float* __restrict__ tab) {
@@ -124,19 +128,21 @@ __global__ void k_alpha_level(int64_t lb, int64_t le, int P, int nb, const NodeW
 #pragma unroll
   for (int b = 0; b < NBP; ++b) {
     float al = 0.0f;
-    if (b < nb && (a1[b] > 0.0f || a2[b] > 0.0f)) al = combine_alpha(a1[b], a2[b], g.w1, g.w12, d);
+    if (b < nb && (a1[b] > 0.0f || a2[b] > 0.0f))
+      al = linear ? 0.5f * (a1[b] + a2[b]) : combine_alpha(a1[b], a2[b], g.w1, g.w12, d);
     tab[(int64_t(iq) * P + p) * NBP + b] = al;
   }
 }
 
-int ensure_table(Tree* t, int nside, cudaStream_t st, Table** out) {
+int ensure_table(Tree* t, int nside, cudaStream_t st, Table** out, bool linear) {
   for (Table& tb : t->tables)
-    if (tb.nside == nside) {
+    if (tb.nside == nside && tb.linear == linear) {
       *out = &tb;
       return TREVR2_OK;
     }
   Table tb;
   tb.nside = nside;
+  tb.linear = linear;
   const int npix = 12 * nside * nside, P = npix / 2;
   T2_CHECK(dalloc(&tb.dirs, npix, st));
   T2_CHECK(dalloc(&tb.dirs64, 3 * size_t(npix), st));
@@ -150,9 +156,9 @@ int ensure_table(Tree* t, int nside, cudaStream_t st, Table** out) {
     unsigned blocks = unsigned((work + 255) / 256);
     if (work == 0) continue;
     switch (t->nbp) {
-      case 1: k_alpha_level<1><<<blocks, 256, 0, st>>>(a, b, P, t->nb, t->nodes, t->int_index, t->alpha_leaf, tb.geo, tb.alpha); note_launch(); break;
-      case 2: k_alpha_level<2><<<blocks, 256, 0, st>>>(a, b, P, t->nb, t->nodes, t->int_index, t->alpha_leaf, tb.geo, tb.alpha); note_launch(); break;
-      default: k_alpha_level<4><<<blocks, 256, 0, st>>>(a, b, P, t->nb, t->nodes, t->int_index, t->alpha_leaf, tb.geo, tb.alpha); note_launch(); break;
+      case 1: k_alpha_level<1><<<blocks, 256, 0, st>>>(a, b, P, t->nb, linear, t->nodes, t->int_index, t->alpha_leaf, tb.geo, tb.alpha); note_launch(); break;
+      case 2: k_alpha_level<2><<<blocks, 256, 0, st>>>(a, b, P, t->nb, linear, t->nodes, t->int_index, t->alpha_leaf, tb.geo, tb.alpha); note_launch(); break;
+      default: k_alpha_level<4><<<blocks, 256, 0, st>>>(a, b, P, t->nb, linear, t->nodes, t->int_index, t->alpha_leaf, tb.geo, tb.alpha); note_launch(); break;
     }
   }
   T2_CUDA(cudaGetLastError());

@@ -570,7 +570,7 @@ extern "C" int trevr2_J(trevr2_tree* tree, const int64_t* active, int64_t A, int
     set_error("trevr2_J: theta must be positive and finite");
     return TREVR2_EINVAL;
   }
-  if (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_ASYNC)) {
+  if (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_ASYNC)) {
     set_error("trevr2_J: unknown flag bits 0x%x", flags);
     return TREVR2_EINVAL;
   }
@@ -593,7 +593,7 @@ extern "C" int trevr2_J(trevr2_tree* tree, const int64_t* active, int64_t A, int
   }
   if (A == 0) return TREVR2_OK;
   Table* tb = nullptr;
-  T2_CHECK(ensure_table(t, nside, st, &tb));
+  T2_CHECK(ensure_table(t, nside, st, &tb, (flags & TREVR2_LINEAR) != 0));
   T2_CHECK(launch_walk(t, tb, active, A, nside, theta, bsel, nbsel, flags, J, st));
   if (flags & TREVR2_ASYNC) return TREVR2_OK;
   return read_status(t, st);
@@ -720,7 +720,7 @@ extern "C" int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const 
               TREVR2_MAX_NSIDE);
     return nside > TREVR2_MAX_NSIDE ? TREVR2_EUNSUPPORTED : TREVR2_EINVAL;
   }
-  if (!(theta > 0.0f) || !std::isfinite(theta) || (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_ASYNC))) {
+  if (!(theta > 0.0f) || !std::isfinite(theta) || (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_ASYNC))) {
     set_error("trevr2_batch_create: theta must be positive and finite, flags SOFT|THICK|ASYNC");
     return TREVR2_EINVAL;
   }
@@ -774,7 +774,7 @@ extern "C" int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const 
     b->trees.push_back(t);
     max_depth = std::max(max_depth, t->max_depth);
     Table* tb = nullptr;
-    int rc = ensure_table(t, nside, st, &tb);
+    int rc = ensure_table(t, nside, st, &tb, (flags & TREVR2_LINEAR) != 0);
     if (rc) return fail(rc);
     fill_walk_args(t, tb, nside, theta, bsel, nb, flags & ~TREVR2_ASYNC, kSrcCapacity, &b->args.tree[i]);
   }
@@ -1082,7 +1082,7 @@ extern "C" int trevr2_J_noalloc(trevr2_tree* tree, const int64_t* active, int64_
     set_error("trevr2_J_noalloc: theta must be positive and finite");
     return TREVR2_EINVAL;
   }
-  if (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_ASYNC)) {
+  if (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_ASYNC)) {
     set_error("trevr2_J_noalloc: unknown flag bits 0x%x", flags);
     return TREVR2_EINVAL;
   }
@@ -1105,11 +1105,16 @@ extern "C" int trevr2_J_noalloc(trevr2_tree* tree, const int64_t* active, int64_
   }
   if (A == 0) return TREVR2_OK;
   Table* tb = nullptr;
+  const bool linear = (flags & TREVR2_LINEAR) != 0;
   for (Table& cand : t->tables)
-    if (cand.nside == nside) tb = &cand;
+    if (cand.nside == nside && cand.linear == linear) tb = &cand;
   if (!tb) {
-    set_error("trevr2_J_noalloc: no tables for nside %d; call trevr2_prepare(tree, %d) first "
-              "(this entry point never allocates)", nside, nside);
+    set_error(linear ? "trevr2_J_noalloc: no linear-average tables for nside %d; make one "
+                       "trevr2_J call with TREVR2_LINEAR and this nside first (this entry point "
+                       "never allocates)"
+                     : "trevr2_J_noalloc: no tables for nside %d; call trevr2_prepare(tree, %d) "
+                       "first (this entry point never allocates)",
+              nside, nside);
     return TREVR2_EINVAL;
   }
   T2_CHECK(launch_walk_noalloc(t, tb, active, A, nside, theta, bsel, nbsel, flags, J, st));
