@@ -1,0 +1,195 @@
+"""Accuracy tests of Sec. 3.3-3.4 on the CPU.
+
+The synthetic geometries (two sources and a cloud, a source between two
+clouds, a source beside a wall) are checked three ways:
+  * the exact-answer code (straight-line optical depth through analytic
+    spheres and half-spaces) against brute-force sampling of the segments
+    and against 1-D quadratures of each geometry written out here;
+  * the exact figures of merit against the "Exact" rows of Table escape,
+    which fixes the reading of each geometry from the text;
+  * the oracle's TREVR2 (transmission and linear averaging) against the
+    table's TREVR2 rows.  Those rows come from a glass and per-bucket rays;
+    here a jittered lattice and per-receiver rays stand in, so the bands are
+    those that separate the table's methods from one another (a few tenths
+    of a percent of escape on the one-source tests), not rounding.
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+LINEAR = 8
+
+
+def _table():
+    rows = {}
+    with open(os.path.join(GOLDEN, "escape_table.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            test, method, esc, cov = line.split()
+            rows[(test, method)] = (float(esc) / 100.0, float(cov))
+    return rows
+
+
+@pytest.fixture(scope="module")
+def esc():
+    from oracle import escape
+    return escape
+
+
+# ----------------------------------------------------------------------------
+# The exact-answer code
+
+def test_chords_match_brute_force_sampling(esc):
+    rng = np.random.default_rng(5)
+    a = rng.uniform(-1, 1, size=(200, 3))
+    b = rng.uniform(-1, 1, size=(200, 3))
+    t = (np.arange(20000) + 0.5) / 20000
+    pts = a[:, None, :] + t[None, :, None] * (b - a)[:, None, :]
+    length = np.linalg.norm(b - a, axis=1)
+    c, R = np.array([0.1, -0.2, 0.05]), 0.45
+    inside = (np.linalg.norm(pts - c, axis=2) < R).mean(axis=1) * length
+    np.testing.assert_allclose(esc.chord_sphere(a, b, c, R), inside, atol=2e-4)
+    p0, n = np.array([0.2, 0.1, -0.1]), np.array([1.0, -2.0, 0.5])
+    inside = (((pts - p0) @ n) >= 0).mean(axis=1) * length
+    np.testing.assert_allclose(esc.chord_halfspace(a, b, p0, n), inside, atol=2e-4)
+
+
+def _wall_quadrature():
+    """Source at distance w = 0.25 from a wall (alpha 10 in 1), r = 2.  A
+    direction at cos(mu) to the wall normal enters it at w/mu."""
+    from scipy import integrate
+    w, r, da = 0.25, 2.0, 9.0
+    mu_w = w / r
+    inner, _ = integrate.quad(lambda mu: math.exp(-da * (r - w / mu)), mu_w, 1.0,
+                              epsabs=1e-13, epsrel=1e-12)
+    escape = math.exp(-r) * (0.5 * (1.0 + mu_w) + 0.5 * inner)
+    mu0 = w / (r - math.log(2.0) / da)  # blocked where 9 (r - w/mu) >= ln 2
+    return escape, 0.5 * (1.0 - mu0)
+
+
+def _clouds_quadrature():
+    """Two clouds of radius 0.1 (alpha 10 in 1) centred 0.25 either side of
+    the source, r = 2.  At angle th to a cloud's axis the chord is
+    2 sqrt(R^2 - (D sin th)^2)."""
+    from scipy import integrate
+    D, R, r, da = 0.25, 0.1, 2.0, 9.0
+    mu_R = math.sqrt(1.0 - (R / D) ** 2)
+
+    def chord(mu):
+        b2 = D * D * (1.0 - mu * mu)
+        return 2.0 * math.sqrt(max(R * R - b2, 0.0))
+
+    inner, _ = integrate.quad(lambda mu: math.exp(-da * chord(mu)), mu_R, 1.0,
+                              epsabs=1e-13, epsrel=1e-12)
+    # each cloud covers the cap mu > mu_R, of solid-angle fraction (1 - mu_R)/2
+    escape = math.exp(-r) * (1.0 - (1.0 - mu_R) + inner)
+    b_max = math.sqrt(R * R - (math.log(2.0) / (2.0 * da)) ** 2)
+    mu_c = math.sqrt(1.0 - (b_max / D) ** 2)
+    return escape, 1.0 - mu_c
+
+
+@pytest.mark.parametrize("name,quad", [("source_wall", _wall_quadrature),
+                                       ("source_two_clouds", _clouds_quadrature)])
+def test_exact_figures_match_quadrature(esc, name, quad):
+    g = workloads.CASES[name]()["geometry"]
+    P = esc.sphere_points(400_000, g["shell_centre"], g["shell_radius"])
+    e, c = esc.figures(esc.exact_J(P, g), P, g)
+    e_q, c_q = quad()
+    assert abs(e - e_q) <= 5e-6 and abs(c - c_q) <= 2e-4, (e, e_q, c, c_q)
+
+
+# ----------------------------------------------------------------------------
+# The geometry against the table's exact rows
+
+@pytest.mark.parametrize("name", ["source_two_clouds", "source_wall"])
+def test_exact_rows_of_the_table(esc, name):
+    rows = _table()
+    g = workloads.CASES[name]()["geometry"]
+    P = esc.sphere_points(400_000, g["shell_centre"], g["shell_radius"])
+    e0, c0 = esc.figures(esc.exact_J(P, g, features=False), P, g)
+    want0 = rows[(name, "exact_nocloud")]
+    assert abs(e0 - math.exp(-2.0)) < 1e-12 and c0 == 0.0
+    assert abs(e0 - want0[0]) <= 5e-5  # 13.53 % printed
+    e, c = esc.figures(esc.exact_J(P, g), P, g)
+    want = rows[(name, "exact")]
+    # the table's exact row was measured on glass particles: within 0.1 %
+    # of escape and 0.01 of covering of the continuous answer
+    assert abs(e - want[0]) <= 1e-3 and abs(c - want[1]) <= 0.01, (e, c, want)
+
+
+def test_two_sources_exact(esc):
+    """No printed exact row with the cloud; the text expects about 98 % to
+    escape, and the table's no-cloud row is 100 %."""
+    rows = _table()
+    g = workloads.two_sources_cloud()["geometry"]
+    P = esc.sphere_points(400_000, g["shell_centre"], g["shell_radius"])
+    e0, c0 = esc.figures(esc.exact_J(P, g, features=False), P, g)
+    assert abs(e0 - rows[("two_sources_cloud", "exact_nocloud")][0]) <= 1e-3 and c0 == 0.0
+    e, _ = esc.figures(esc.exact_J(P, g), P, g)
+    assert 0.97 <= e <= 0.99, e
+
+
+@pytest.mark.parametrize("name", ["two_sources_cloud", "source_two_clouds", "source_wall"])
+def test_shell_receivers_sample_the_sphere(esc, name):
+    """The shell of lattice receivers gives the continuous sphere's exact
+    figures to within its sampling noise (about 1 % of escape)."""
+    case = workloads.CASES[name]()
+    g = case["geometry"]
+    pts = case["pos"][case["active"]]
+    r = np.linalg.norm(pts - g["shell_centre"], axis=1)
+    assert len(pts) > 5000 and np.all(np.abs(r - g["shell_radius"]) < 0.13)
+    assert np.all(case["mass"][case["active"]] > 0)  # receivers are gas
+    P = esc.sphere_points(200_000, g["shell_centre"], g["shell_radius"])
+    e_s, c_s = esc.figures(esc.exact_J(P, g), P, g)
+    e, c = esc.figures(esc.exact_J(pts, g), pts, g)
+    assert abs(e - e_s) <= 0.01 * e_s and abs(c - c_s) <= 0.01, (e, e_s, c, c_s)
+
+
+# ----------------------------------------------------------------------------
+# The method against the table's TREVR2 rows
+
+BANDS = {
+    # (escape, covering) half-widths around the printed row
+    ("source_two_clouds", "transmission"): (0.003, 0.005),
+    ("source_two_clouds", "linear"): (0.003, 0.005),
+    ("source_wall", "transmission"): (0.003, 0.03),
+    ("source_wall", "linear"): (0.003, 0.03),
+    ("two_sources_cloud", "transmission"): (0.03, 0.03),
+}
+
+
+@pytest.fixture(scope="module")
+def oracle_figures(oracle_mod, esc):
+    out = {}
+    for name in ("two_sources_cloud", "source_two_clouds", "source_wall"):
+        case = workloads.CASES[name]()
+        ot = oracle_mod.OracleTree.from_case(case)
+        pts = case["pos"][case["active"]]
+        for method, flags in (("transmission", 0), ("linear", LINEAR)):
+            J = ot.J(case["active"], case["nside"], case["theta"], flags=flags)[:, 0]
+            out[(name, method)] = esc.figures(J, pts, case["geometry"])
+    return out
+
+
+@pytest.mark.parametrize("key", sorted(BANDS))
+def test_oracle_matches_table_rows(oracle_figures, key):
+    e, c = oracle_figures[key]
+    want = _table()[key]
+    de, dc = BANDS[key]
+    assert abs(e - want[0]) <= de and abs(c - want[1]) <= dc, (key, e, c, want)
+
+
+def test_linear_average_fails_on_the_combined_cloud(oracle_figures):
+    """Sec. 3.3: once the sources and the dense cloud share a cell the
+    linear average wipes out most of the flux at r = 6 (the table prints
+    33.7 %, covering 0.684), while the transmission average keeps it."""
+    e_l, c_l = oracle_figures[("two_sources_cloud", "linear")]
+    e_t, _ = oracle_figures[("two_sources_cloud", "transmission")]
+    assert e_l < 0.5 and c_l > 0.5 and e_t - e_l > 0.4, (e_l, c_l, e_t)

@@ -27,6 +27,15 @@ Recipes (section numbers are the paper's):
     sit in dense gas, Sec. 5).
 The galaxy snapshot of Sec. 3.1 is not available; the clumpy 128^3 field
 stands in for its shape.
+
+The three accuracy geometries of Sec. 3.3-3.4 (two sources and a cloud, a
+source between two clouds, a source beside a wall) are built from the sizes
+the text gives.  A jittered lattice of the stated spacing stands in for the
+glass; every gas element has unit density (m = spacing^3, h = spacing) and
+kappa equal to the absorption coefficient alpha at its position, so the
+bucket absorption sum(kappa m)/V is alpha wherever a leaf is filled evenly.
+Their dicts also carry the geometry (sources, absorbing features, shell
+radius) so that the exact answer can be evaluated next to the method's.
 """
 
 from __future__ import annotations
@@ -43,6 +52,9 @@ __all__ = [
     "adjoint_case",
     "batched_cases",
     "random_case",
+    "two_sources_cloud",
+    "source_two_clouds",
+    "source_wall",
     "CASES",
 ]
 
@@ -221,9 +233,112 @@ def random_case(n_gas: int, n_src: int, nb: int = 1, seed: int = 0, nside: int =
                  nside=nside, theta=theta, bucket=bucket)
 
 
+def jittered_block(lo, spacing: float, cells: int, rng: np.random.Generator) -> np.ndarray:
+    """cells^3 points, one per cubic cell of side `spacing` starting at `lo`,
+    each jittered by U(-1/4, 1/4) of a cell per axis."""
+    return np.asarray(lo, dtype=np.float64) + jittered_lattice(cells, rng) * (cells * spacing)
+
+
+def _accuracy_case(name, gpos, spacing, alpha, spos, slum, box_lo, box_size, shell_centre,
+                   shell_radius, shell_width, geometry):
+    """Unit-density gas (m = s^3, h = s, kappa = alpha) plus point sources;
+    the receivers are the gas elements within shell_width/2 of the sphere of
+    radius shell_radius about shell_centre."""
+    ng = gpos.shape[0]
+    pos, mass, kappa, lum, h = _gas_plus_sources(
+        gpos, spacing ** 3, spacing, [1.0], spos, slum)
+    kappa[:ng, 0] = alpha
+    r = np.linalg.norm(gpos - np.asarray(shell_centre)[None, :], axis=1)
+    active = np.flatnonzero(np.abs(r - shell_radius) < 0.5 * shell_width)
+    case = _pack(name, pos, mass, kappa, lum, h, active, nside=2, theta=0.75)
+    case["box_lo"] = np.asarray(box_lo, dtype=np.float64)
+    case["box_size"] = float(box_size)
+    case["geometry"] = dict(geometry, sources=np.asarray(spos, dtype=np.float64),
+                            L=np.asarray(slum, dtype=np.float64),
+                            shell_centre=np.asarray(shell_centre, dtype=np.float64),
+                            shell_radius=float(shell_radius))
+    return case
+
+
+def two_sources_cloud(seed: int = 1050):
+    """Cloud irradiated by two sources (Sec. 3.3): a sphere of radius 0.5 at
+    the origin with alpha = 1e4 (spacing 0.0625) in a medium with alpha =
+    1e-4 (spacing 0.25); L = 0.5 sources at (-2, 0, 0) and (0, -2, 0).  The
+    volume is a cube of side 17 centred on (-2.1, -2.1, -2.1), so that the
+    sources and the cloud share a cell of side 4.25; the receivers are the gas
+    elements on the sphere r = 6 about the origin."""
+    rng = np.random.default_rng(seed)
+    side, s_out, s_in, R = 17.0, 0.25, 0.0625, 0.5
+    lo = np.full(3, -2.1 - 0.5 * side)
+    outer = jittered_block(lo, s_out, int(round(side / s_out)), rng)
+    outer = outer[np.linalg.norm(outer, axis=1) >= R]
+    inner = jittered_block(np.full(3, -R), s_in, int(round(2 * R / s_in)), rng)
+    inner = inner[np.linalg.norm(inner, axis=1) < R]
+    gpos = np.concatenate([outer, inner])
+    spacing = np.concatenate([np.full(len(outer), s_out), np.full(len(inner), s_in)])
+    alpha = np.concatenate([np.full(len(outer), 1e-4), np.full(len(inner), 1e4)])
+    spos = np.array([[-2.0, 0.0, 0.0], [0.0, -2.0, 0.0]])
+    geometry = {"alpha_bg": 1e-4,
+                "features": [("sphere", np.zeros(3), R, 1e4)]}
+    return _accuracy_case("two_sources_cloud", gpos, spacing, alpha, spos, [0.5, 0.5],
+                          lo, side, np.zeros(3), 6.0, s_out, geometry)
+
+
+def _offset_source_gas(rng):
+    """Sec. 3.4 particles: a sphere of radius 2.5 about the origin at spacing
+    0.0625, refined to 0.8/38 (the text's 0.0209) within 0.4 of the source at
+    (0.17, 0.17, 0.17)."""
+    src = np.full(3, 0.17)
+    R_vol, s_out, r_in = 2.5, 0.0625, 0.4
+    n_in = 38
+    s_in = 2 * r_in / n_in
+    outer = jittered_block(np.full(3, -R_vol), s_out, int(round(2 * R_vol / s_out)), rng)
+    outer = outer[(np.linalg.norm(outer, axis=1) < R_vol)
+                  & (np.linalg.norm(outer - src, axis=1) >= r_in)]
+    inner = jittered_block(src - r_in, s_in, n_in, rng)
+    inner = inner[np.linalg.norm(inner - src, axis=1) < r_in]
+    gpos = np.concatenate([outer, inner])
+    spacing = np.concatenate([np.full(len(outer), s_out), np.full(len(inner), s_in)])
+    return src, gpos, spacing, s_out
+
+
+def source_two_clouds(seed: int = 1051):
+    """A source flanked by two clouds (Sec. 3.4.1): alpha = 1 medium, clouds
+    of radius 0.1 with alpha = 10 at 0.25 either side of the L = 1 source
+    along the main diagonal; receivers on the sphere r = 2 about the source."""
+    rng = np.random.default_rng(seed)
+    src, gpos, spacing, s_out = _offset_source_gas(rng)
+    n = np.full(3, 1.0 / np.sqrt(3.0))
+    centres = [src + 0.25 * n, src - 0.25 * n]
+    alpha = np.ones(len(gpos))
+    for c in centres:
+        alpha[np.linalg.norm(gpos - c, axis=1) < 0.1] = 10.0
+    geometry = {"alpha_bg": 1.0,
+                "features": [("sphere", c, 0.1, 10.0) for c in centres]}
+    return _accuracy_case("source_two_clouds", gpos, spacing, alpha, src[None, :], [1.0],
+                          np.full(3, -2.5), 5.0, src, 2.0, s_out, geometry)
+
+
+def source_wall(seed: int = 1051):
+    """A source beside a wall (Sec. 3.4.2): the particles of the two-cloud
+    case; alpha = 10 in the half-space beyond the plane 0.25 from the source
+    along -(1, 1, 1)/sqrt(3), alpha = 1 elsewhere."""
+    rng = np.random.default_rng(seed)
+    src, gpos, spacing, s_out = _offset_source_gas(rng)
+    n = -np.full(3, 1.0 / np.sqrt(3.0))  # from the source towards the wall
+    p0 = src + 0.25 * n
+    alpha = np.where((gpos - p0) @ n >= 0.0, 10.0, 1.0)
+    geometry = {"alpha_bg": 1.0, "features": [("halfspace", p0, n, 10.0)]}
+    return _accuracy_case("source_wall", gpos, spacing, alpha, src[None, :], [1.0],
+                          np.full(3, -2.5), 5.0, src, 2.0, s_out, geometry)
+
+
 CASES = {
     "uniform_point_source": uniform_point_source,
     "stromgren_like": stromgren_like,
     "clumpy_multiband": clumpy_multiband,
     "adjoint_case": adjoint_case,
+    "two_sources_cloud": two_sources_cloud,
+    "source_two_clouds": source_two_clouds,
+    "source_wall": source_wall,
 }
