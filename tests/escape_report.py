@@ -1,0 +1,129 @@
+"""Accuracy report for the tests of Sec. 3.3-3.4 (Table escape), GPU path.
+
+For each geometry and each absorption average it builds the tree on the
+GPU, computes J on the shell receivers and on every gas element, derives the
+escape fraction and covering factor on the shell, and prints them beside the
+paper's printed row, the exact answer and the oracle's figures, with the
+GPU times (CUDA events on the launching stream, median of 10 after 3
+warm-up calls; the build includes the host-to-device copy of the inputs).
+
+    python tests/escape_report.py [--out FILE]
+
+Needs a CUDA device; the oracle runs on the host for the shell only.
+"""
+
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+LINEAR = 8
+NAMES = ["two_sources_cloud", "source_two_clouds", "source_wall"]
+
+
+def _table():
+    rows = {}
+    with open(os.path.join(HERE, "golden", "escape_table.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            test, method, e, c = line.split()
+            rows[(test, method)] = (float(e) / 100.0, float(c))
+    return rows
+
+
+def _time(fn, reps=10, warmup=3):
+    for _ in range(warmup):
+        fn()
+    st = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=None, help="also write the rows as JSON lines here")
+    args = ap.parse_args()
+
+    import oracle
+    from oracle import escape as esc
+    import paper_2310_15235_gb300 as t2
+
+    t2.load_library()
+    table = _table()
+    rows = []
+    for name in NAMES:
+        case = workloads.CASES[name]()
+        g = case["geometry"]
+        act = case["active"]
+        pts = case["pos"][act]
+        gas = np.flatnonzero(case["mass"] > 0)
+        ot = oracle.OracleTree.from_case(case)
+        build = lambda: t2.build(case["pos"], case["mass"], case["kappa"], case["lum"],  # noqa: E731
+                                 case["h"], case["box_lo"], case["box_size"], case["bucket"])
+        trees = []
+        t_build = _time(lambda: trees.append(build()))
+        for tr in trees[:-1]:
+            tr.free()
+        tree = trees[-1]
+        e_x, c_x = esc.figures(esc.exact_J(pts, g), pts, g)
+        act_d = torch.as_tensor(act, device="cuda")
+        gas_d = torch.as_tensor(gas, device="cuda")
+        for method, flags in (("transmission", 0), ("linear", LINEAR)):
+            J = tree.J(act_d, case["nside"], case["theta"], flags=flags).cpu().numpy()[:, 0]
+            e, c = esc.figures(J, pts, g)
+            e_o, c_o = esc.figures(ot.J(act, case["nside"], case["theta"], flags=flags)[:, 0],
+                                   pts, g)
+            t_shell = _time(lambda: tree.J(act_d, case["nside"], case["theta"], flags=flags))
+            t_all = _time(lambda: tree.J(gas_d, case["nside"], case["theta"], flags=flags))
+            paper = table.get((name, method), (float("nan"), float("nan")))
+            rows.append(dict(test=name, method=method, elements=len(case["pos"]),
+                             shell=len(act), escape=e, covering=c, oracle_escape=e_o,
+                             oracle_covering=c_o, exact_escape=e_x, exact_covering=c_x,
+                             paper_escape=paper[0], paper_covering=paper[1],
+                             build_ms=t_build, shell_ms=t_shell, all_gas_ms=t_all,
+                             all_gas=len(gas)))
+        tree.free()
+
+    print("| test | average | escape GPU | oracle | paper | covering GPU | oracle | paper "
+          "| exact escape / covering |")
+    print("|---|---|---|---|---|---|---|---|---|")
+    for r in rows:
+        print(f"| {r['test']} | {r['method']} | {100 * r['escape']:.2f} % "
+              f"| {100 * r['oracle_escape']:.2f} % | {100 * r['paper_escape']:.2f} % "
+              f"| {r['covering']:.3f} | {r['oracle_covering']:.3f} | {r['paper_covering']:.3f} "
+              f"| {100 * r['exact_escape']:.2f} % / {r['exact_covering']:.3f} |")
+    print()
+    print("| test | average | elements | build ms | shell receivers | J ms | all gas | J ms "
+          "| all-gas receivers/s |")
+    print("|---|---|---|---|---|---|---|---|---|")
+    for r in rows:
+        print(f"| {r['test']} | {r['method']} | {r['elements']} | {r['build_ms']:.2f} "
+              f"| {r['shell']} | {r['shell_ms']:.3f} | {r['all_gas']} | {r['all_gas_ms']:.2f} "
+              f"| {r['all_gas'] / (r['all_gas_ms'] * 1e-3):.3e} |")
+    if args.out:
+        with open(args.out, "w") as f:
+            for r in rows:
+                f.write(json.dumps(r) + "\n")
+
+
+if __name__ == "__main__":
+    main()
