@@ -32,6 +32,7 @@ _lib = None
 FLAG_SOFT = 1
 FLAG_THICK = 2
 FLAG_LINEAR = 8
+FLAG_BUCKET = 16
 
 
 def build(force: bool = False) -> str:

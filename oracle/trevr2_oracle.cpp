@@ -43,6 +43,13 @@
 //  R9 FLAG_LINEAR replaces Eq. transmissionavg by the volume-weighted linear
 //     average of the two halves' absorption, the scheme Sec. 2.6 compares
 //     it with; it is direction independent (the same value in every pair).
+//  R10 FLAG_BUCKET (per-bucket beams, Sec. 2 and Sec. 2.5.1): the walk starts
+//     from the centre of the receiver's bucket (the geometric centre of its
+//     leaf box), so every receiver of a bucket shares the cut, the beam of
+//     each source and the projected distance s.  Per receiver, the optical
+//     depth up to s is multiplied by r/s with r the receiver's own distance
+//     to the source, and the kernel is g(r).  A source at the bucket centre
+//     itself has no beam and is skipped, as one on top of a receiver is.
 
 #include <algorithm>
 #include <atomic>
@@ -542,7 +549,7 @@ bool ray_chord(const double x[3], const double n[3], const double blo[3], const 
   return t1 > t0;
 }
 
-enum : uint32_t { FLAG_SOFT = 1u, FLAG_THICK = 2u, FLAG_LINEAR = 8u };
+enum : uint32_t { FLAG_SOFT = 1u, FLAG_THICK = 2u, FLAG_LINEAR = 8u, FLAG_BUCKET = 16u };
 
 struct WalkStats {
   int64_t visited = 0;   // nodes given the opening test
@@ -565,6 +572,7 @@ struct Problem {
   double h_default;
   std::vector<double> dirs;   // [npix][3]
   std::vector<int64_t> pair;  // [npix]
+  std::vector<int64_t> leaf_of;  // [N] original index -> its leaf (FLAG_BUCKET)
 };
 
 // J of one receiver, every band (Sec. 2.5).
@@ -576,6 +584,14 @@ void walk_receiver(const Problem<T>& pr, int64_t i_orig, T* Jout, WalkStats* st)
   const int64_t npix = 12 * static_cast<int64_t>(pr.nside) * pr.nside;
   const int64_t P = npix / 2;
   const double* xi = &t.pos[3 * i_orig];
+  // R10: with per-bucket beams the walk's origin is the centre of the
+  // receiver's leaf box, otherwise the receiver itself.
+  double xo[3] = {xi[0], xi[1], xi[2]};
+  if (pr.flags & FLAG_BUCKET) {
+    double blo[3], bhi[3];
+    node_box(t.nodes[pr.leaf_of[i_orig]], t.lo, t.size, blo, bhi);
+    for (int a = 0; a < 3; ++a) xo[a] = 0.5 * (blo[a] + bhi[a]);
+  }
   struct CutCell {
     int64_t node;
     double lo[3], hi[3];
@@ -603,7 +619,7 @@ void walk_receiver(const Problem<T>& pr, int64_t i_orig, T* Jout, WalkStats* st)
     cc.node = q;
     node_box(nd, t.lo, t.size, cc.lo, cc.hi);
     ++ws.visited;
-    bool open = cell_opens(xi, cc.lo, cc.hi, ag.B[q], pr.theta);
+    bool open = cell_opens(xo, cc.lo, cc.hi, ag.B[q], pr.theta);
     if (!open) {
       cut.push_back(cc);
       if (val(ag.Ltot[q]) > 0.0) {
@@ -642,26 +658,29 @@ void walk_receiver(const Problem<T>& pr, int64_t i_orig, T* Jout, WalkStats* st)
     const double* nk = &pr.dirs[3 * k];
     for (const CutCell& cc : cut) {
       double t0, t1;
-      if (!ray_chord(xi, nk, cc.lo, cc.hi, t0, t1)) continue;
+      if (!ray_chord(xo, nk, cc.lo, cc.hi, t0, t1)) continue;
       segs[k].push_back({t0, t1, &(*pr.tab)[(cc.node * P + pr.pair[k]) * nb]});
       ++ws.segments;
     }
   }
 
-  // Sec. 2.5.1: a source joins the one beam holding its direction; the
-  // optical depth along that beam up to the projected distance s is scaled
-  // by r/s; the source adds L e^{-tau} g(r) (R6, Eq. intint with SOFT).
+  // Sec. 2.5.1: a source joins the one beam holding its direction (from the
+  // walk's origin); the optical depth along that beam up to the projected
+  // distance s is scaled by r/s, r the receiver's distance to the source; the
+  // source adds L e^{-tau} g(r) (R6, Eq. intint with SOFT).
   const double hi_ = t.h.empty() ? pr.h_default : t.h[i_orig];
   for (int b = 0; b < nb; ++b) Jout[b] = T(0.0);
   for (const Src& s : srcs) {
+    T vo[3] = {s.p[0] - xo[0], s.p[1] - xo[1], s.p[2] - xo[2]};
+    if (val(vo[0]) == 0.0 && val(vo[1]) == 0.0 && val(vo[2]) == 0.0) continue;
+    double vv[3] = {val(vo[0]), val(vo[1]), val(vo[2])};
+    int64_t k = vec2pix_ring(pr.nside, vv);
+    const double* nk = &pr.dirs[3 * k];
+    T sp = vo[0] * nk[0] + vo[1] * nk[1] + vo[2] * nk[2];
+    if (!(val(sp) > 0.0)) continue;  // cannot happen: beam radius < 90 degrees
     T v[3] = {s.p[0] - xi[0], s.p[1] - xi[1], s.p[2] - xi[2]};
     T r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     if (val(r) == 0.0) continue;
-    double vv[3] = {val(v[0]), val(v[1]), val(v[2])};
-    int64_t k = vec2pix_ring(pr.nside, vv);
-    const double* nk = &pr.dirs[3 * k];
-    T sp = v[0] * nk[0] + v[1] * nk[1] + v[2] * nk[2];
-    if (!(val(sp) > 0.0)) continue;  // cannot happen: beam radius < 90 degrees
     ++ws.sources;
     T g = (pr.flags & FLAG_SOFT) ? soft_kernel(r, hi_) : T(1.0) / (4.0 * kPi * r * r);
     for (int b = 0; b < nb; ++b) {
@@ -708,6 +727,15 @@ Problem<T> make_problem(const Tree& t, const Aggregates<T>& ag, const std::vecto
   for (int64_t k = 0; k < npix; ++k) {
     pix2vec_ring(nside, k, &pr.dirs[3 * k]);
     pr.pair[k] = pair_of_pixel(nside, k);
+  }
+  if (flags & FLAG_BUCKET) {
+    pr.leaf_of.assign(t.N, -1);
+    for (size_t q = 0; q < t.nodes.size(); ++q) {
+      const Node& nd = t.nodes[q];
+      if (nd.child >= 0) continue;
+      for (int64_t e = nd.first; e < nd.first + nd.count; ++e)
+        pr.leaf_of[t.perm[e]] = static_cast<int64_t>(q);
+    }
   }
   return pr;
 }

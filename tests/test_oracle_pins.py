@@ -650,3 +650,113 @@ def test_linear_average_never_lets_more_through(oracle_mod):
     assert np.all(Jl <= Jt * (1 + 1e-12))
     assert ((Jt - Jl) / Jt).max() > 1e-2  # accepted internal cells differ
     assert (lin > tr * 1.01).any()
+
+
+# ----------------------------------------------------------------------------
+# Per-bucket beams (Sec. 2 and Sec. 2.5.1, flag BUCKET): the walk starts from
+# the centre of the receiver's bucket; each receiver scales the beam's
+# optical depth by its own distance over the projected one.
+
+def _leaf_centres(t, n):
+    """Centre of the leaf box holding each element (original order)."""
+    e = t.export()
+    out = np.empty((n, 3))
+    for q in np.flatnonzero(e["child"] < 0):
+        idx = e["perm"][e["first"][q]: e["first"][q] + e["count"][q]]
+        out[idx] = 0.5 * (e["box"][q, :3] + e["box"][q, 3:])
+    return out
+
+
+@pytest.mark.parametrize("n_gas,n_src,nb,seed,bucket,soft", [
+    (150, 9, 2, 1, 12, False), (97, 31, 3, 2, 3, False), (64, 5, 1, 3, 1, True),
+    (300, 12, 1, 5, 12, True),
+])
+def test_bucket_brute_force_theta0(oracle_mod, n_gas, n_src, nb, seed, bucket, soft):
+    """kappa = 0, theta -> 0: every receiver of a bucket still gets the
+    direct sum over all other sources at its own distance (Eq. intint with
+    its own h under SOFT)."""
+    case = workloads.random_case(n_gas, n_src, nb=nb, seed=seed, clumped=True, bucket=bucket,
+                                 n_active=(n_gas + n_src) // 2)
+    case["kappa"][:] = 0.0
+    t = oracle_mod.OracleTree.from_case(case)
+    flags = oracle_mod.FLAG_BUCKET | (oracle_mod.FLAG_SOFT if soft else 0)
+    J = t.J(case["active"], 2, 1e-9, flags=flags)
+    np.testing.assert_allclose(J, _brute_J(case, soft=soft), rtol=1e-11, atol=1e-300)
+
+
+@pytest.mark.parametrize("nside,theta", [(2, 0.75), (1, 0.3), (4, 1.5), (2, 0.5)])
+def test_bucket_closed_form_one_source(oracle_mod, nside, theta):
+    """One source in a uniform medium: tau along the bucket's beam is
+    kappa rho s, scaled by r/s it is kappa rho r, so every receiver gets
+    L e^{-kappa rho r} / (4 pi r^2) at its own r, whenever the beam from its
+    bucket centre to the projected source point stays inside the box."""
+    case = workloads.uniform_point_source(offset=True)
+    t = oracle_mod.OracleTree.from_case(case)
+    J = t.J(case["active"], nside, theta, flags=oracle_mod.FLAG_BUCKET)
+    src = case["pos"][-1]
+    centres = _leaf_centres(t, len(case["pos"]))
+    dirs = oracle_mod.pix2vec(nside)
+    ok = np.ones(len(case["active"]), dtype=bool)
+    for a, i in enumerate(case["active"]):
+        v = src - centres[i]
+        k = oracle_mod.vec2pix(nside, v[None])[0]
+        q = centres[i] + (v @ dirs[k]) * dirs[k]
+        ok[a] = np.all(q >= 0) and np.all(q < 1)
+    assert ok.mean() > 0.9
+    r = np.linalg.norm(case["pos"][case["active"]] - src, axis=1)
+    np.testing.assert_allclose(J[ok, 0], np.exp(-2.0 * r[ok]) / (4 * np.pi * r[ok] ** 2),
+                               rtol=1e-12)
+    # the bucket's beams differ from the receivers' own: somewhere J differs
+    J1 = t.J(case["active"], nside, theta)
+    assert np.abs(J - J1).max() > 0 or not (~ok).any()
+
+
+@pytest.mark.parametrize("flags", [0, 1, 2, 3, 8])
+def test_bucket_equals_per_receiver_at_leaf_centres(oracle_mod, flags):
+    """Elements at the centres of an 8^3 grid with bucket 1: each leaf holds
+    one element at its own box centre, so the per-bucket walk starts where
+    the per-receiver walk does and the two agree exactly."""
+    rng = np.random.default_rng(91)
+    idx = np.arange(8, dtype=np.float64)
+    g = np.stack(np.meshgrid(idx, idx, idx, indexing="ij"), -1).reshape(-1, 3)
+    pos = (g + 0.5) / 8
+    n = len(pos)
+    mass = rng.uniform(0.5, 1.5, n) / n
+    kappa = rng.uniform(0.0, 40.0, (n, 2))
+    lum = np.where(rng.uniform(size=(n, 1)) < 0.1, rng.uniform(0.1, 1.0, (n, 2)), 0.0)
+    h = np.full(n, 1.0 / 8)
+    case = workloads._pack("grid", pos, mass, kappa, lum, h, np.arange(n), 2, 0.75, bucket=1)
+    t = oracle_mod.OracleTree.from_case(case)
+    np.testing.assert_array_equal(_leaf_centres(t, n), pos)
+    for nside, theta in [(2, 0.75), (4, 0.5)]:
+        J0 = t.J(case["active"], nside, theta, flags=flags)
+        J1 = t.J(case["active"], nside, theta, flags=flags | oracle_mod.FLAG_BUCKET)
+        np.testing.assert_allclose(J1, J0, rtol=1e-13, atol=1e-300)
+
+
+def test_bucket_receivers_share_the_beam(oracle_mod):
+    """One source, clumpy absorbers: within a bucket every receiver sees the
+    same beam optical depth per unit projected distance, tau/s =
+    -ln(4 pi r^2 J / L) / r, while the per-receiver walk gives each its own."""
+    case = workloads.random_case(3000, 0, nb=1, seed=93, clumped=True, kappa_scale=40.0,
+                                 bucket=12)
+    n = len(case["pos"])
+    case["lum"][7, 0] = 1.0  # one luminous gas element
+    case["active"] = np.arange(n)
+    t = oracle_mod.OracleTree.from_case(case)
+    e = t.export()
+    leaves = np.flatnonzero((e["child"] < 0) & (e["count"] >= 6))
+    src = case["pos"][7]
+    shared = []
+    for flags in (oracle_mod.FLAG_BUCKET, 0):
+        spread = []
+        for q in leaves[:40]:
+            members = e["perm"][e["first"][q]: e["first"][q] + e["count"][q]]
+            members = members[members != 7]
+            J = t.J(members, 2, 0.75, flags=flags)[:, 0]
+            r = np.linalg.norm(case["pos"][members] - src, axis=1)
+            per = -np.log(4 * np.pi * r * r * J) / r
+            spread.append(per.max() - per.min())
+        shared.append(np.array(spread))
+    assert np.all(shared[0] <= 1e-9 * 40.0)
+    assert shared[1].max() > 1e-3
