@@ -52,6 +52,10 @@ extern "C" {
 #define TREVR2_LINEAR 8u /* internal cells take the volume-weighted linear average of
                             their halves' absorption, the scheme Sec. 2.6 compares
                             Eq. transmissionavg with (direction independent) */
+#define TREVR2_BUCKET 16u /* per-bucket beams (Sec. 2, Sec. 2.5.1): one walk per
+                             leaf holding receivers, from its box centre; each
+                             receiver scales the beam optical depth by its own
+                             distance over the projected one (trevr2_J only) */
 
 /* Supported sizes: 1 <= nb <= 4 bands; nside a power of two in [1, 16];
  * N < 2^31 elements; 1 <= bucket <= 4096. */
@@ -101,7 +105,16 @@ int trevr2_build(const double* pos, const float* mass, const float* kappa, const
  *          and cached
  *  theta   opening parameter theta_rad > 0 (paper default 0.75)
  *  bands   host [nbsel] band indices to return, or NULL = all nb bands
- *  flags   TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_ASYNC
+ *  flags   TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_BUCKET |
+ *          TREVR2_ASYNC.  With TREVR2_BUCKET the cut, the beam of each source,
+ *          its projected distance s and the optical depth to s are those of
+ *          the centre of the leaf box holding the receiver, shared by every
+ *          receiver of that leaf; each receiver adds L g(r) e^{-tau r/s} with
+ *          r its own distance to the source (its own h and Eq. taucorr
+ *          factor under TREVR2_SOFT / TREVR2_THICK).  A source exactly at a
+ *          bucket centre has no beam and is skipped.  trevr2_J_backward,
+ *          the batches and trevr2_J_noalloc do not take this flag
+ *          (EUNSUPPORTED, EUNSUPPORTED, EINVAL).
  *  J       [A][nbsel] float32 output, overwritten
  * Active indices outside [0, N) give EINVAL (their rows are set to NaN).
  * Without TREVR2_ASYNC the call synchronises `stream` and returns any device

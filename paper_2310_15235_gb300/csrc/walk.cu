@@ -43,7 +43,7 @@ namespace trevr2 {
 // crossed far halves go on the stack.  The stack walk then takes the far
 // halves, nearest first.  This visits the same cells in the same order as a
 // walk from the root.
-template <int NBP>
+template <int NBP, bool kBucket = false>
 __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int* lstk,
                              const SrcEntry* V, float* T, const int* off, const int* order,
                              int nbeams, int* next_beam, const NodeW* chain, int leaf) {
@@ -110,7 +110,7 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
       const NodeW nd = a.nodes[q];
       float t0, t1;
       if (!beam_chord(nd, xv, n, inv, smax, t0, t1)) continue;
-      if (!(nd.meta & kMetaLeaf) && cell_opens(a, q, nd, x, si)) {
+      if (!(nd.meta & kMetaLeaf) && cell_opens<kBucket>(a, q, nd, x, si)) {
         // the crossed halves, the near one (the side of the receiver) on top
         bool lower_first, lower_hit, upper_hit;
         float lt0, lt1, ut0, ut1;
@@ -250,6 +250,202 @@ __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk(Wa
     const int64_t r = a.order ? int64_t(a.order[slot]) : int64_t(slot);
     walk_receiver<NBP>(a, a.active[r], a.J + r * a.nbsel, lane, stk, off, next_beam,
                        lstk, U, Up, V, T);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-bucket beams (TREVR2_BUCKET; Sec. 2 and Sec. 2.5.1).  One walk per
+// bucket, the leaf that holds the receivers, from the centre of its box:
+// the cut, each source's beam and projected distance s and the optical depth
+// tau_k(s) are the bucket's.  Each receiver of the bucket then adds
+// L g(r) e^{-tau_k(s) r/s} at its own distance r (its own h under
+// TREVR2_SOFT, its own Eq. taucorr factor under TREVR2_THICK).  Receivers
+// come in Morton order, so a bucket's receivers are adjacent; the warp that
+// takes a bucket's first slot walks it, and other slots are passed over.
+
+struct BucketArgs {
+  const uint64_t* keys;  // [A] sorted element position of each slot (N: invalid)
+  const int* leaf;       // [A] leaf of each slot (-1: invalid)
+  uint32_t rflags;       // the receivers' flags (TREVR2_SOFT, TREVR2_THICK)
+};
+
+// The leaf holding each slot's element: down the tree by the first element
+// of each upper half.
+__global__ void k_bucket_leaf(const int* __restrict__ child, const int* __restrict__ first,
+                              const uint64_t* __restrict__ keys, int64_t A, int64_t N,
+                              int* __restrict__ leaf) {
+  const int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (p >= A) return;
+  const int64_t si = int64_t(keys[p]);
+  if (si >= N) {
+    leaf[p] = -1;
+    return;
+  }
+  int q = 0;
+  for (int c = child[0]; c >= 0; c = child[q]) q = si < first[c + 1] ? c : c + 1;
+  leaf[p] = q;
+}
+
+// The staged sources against the bucket's receivers (one per lane j < nrec,
+// position xr, size hr): per receiver, all lanes over the sources with a
+// compensated FP32 sum, reduced in FP64 into acc of lane j.
+template <int NBP>
+__device__ __forceinline__ void eval_bucket(const WalkArgs& a, bool soft, int lane,
+                                            const SrcEntry* V, const float* T, int n, int nrec,
+                                            float4 xr, float hr, double* acc) {
+  for (int j = 0; j < nrec; ++j) {
+    const float xx = __shfl_sync(0xffffffffu, xr.x, j);
+    const float xy = __shfl_sync(0xffffffffu, xr.y, j);
+    const float xz = __shfl_sync(0xffffffffu, xr.z, j);
+    const float hh = __shfl_sync(0xffffffffu, hr, j);
+    float Js[NBP], Jc[NBP];
+#pragma unroll
+    for (int b = 0; b < NBP; ++b) Js[b] = Jc[b] = 0.0f;
+    for (int e = lane; e < n; e += 32) {
+      const SrcEntry src = V[e];
+      const bool elem = (src.ref & kRefElement) != 0;
+      const int64_t id = src.ref & 0x7fffffff;
+      const float4 p = elem ? a.pos32[id] : a.csrc[id];
+      const float vx = p.x - xx, vy = p.y - xy, vz = p.z - xz;
+      const float r2 = vx * vx + vy * vy + vz * vz;
+      if (!(r2 > 0.0f)) continue;  // the receiver itself, or on top of it
+      const float r = sqrtf(r2);
+      const float w = soft ? soft_kernel(r, hh) : 1.0f / (kFourPi * r2);
+      const float rs = r / src.s;
+      const BandVec<NBP> L = load_bands<NBP>(elem ? a.Lelem + id * NBP : a.Lnode + id * NBP);
+      const BandVec<NBP> tk = load_bands<NBP>(T + int64_t(e) * NBP);
+#pragma unroll
+      for (int b = 0; b < NBP; ++b) {
+        const float term = L.v[b] * w * expf(-tk.v[b] * rs);
+        const float y = term - Jc[b];
+        const float t = Js[b] + y;
+        Jc[b] = (t - Js[b]) - y;
+        Js[b] = t;
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < NBP; ++b) {
+      double v = double(Js[b]) - double(Jc[b]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == j) acc[b] += v;
+    }
+  }
+}
+
+// J of the receivers in slots [p0, p1), all in leaf q, into their rows.
+template <int NBP>
+__device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0, int64_t p1,
+                            int q, int64_t gw, int lane, int* stk, int* off, int* next_beam,
+                            int* lstk, SrcEntry* U, int* Up, SrcEntry* V, float* T) {
+  if (q < 0) {  // receivers outside [0, N): NaN rows and a status bit
+    for (int64_t p = p0 + lane; p < p1; p += 32)
+      for (int c = 0; c < a.nbsel; ++c) a.J[int64_t(a.order[p]) * a.nbsel + c] = __int_as_float(0x7fc00000);
+    if (lane == 0) atomicOr(a.status, kStatusBadActive);
+    return;
+  }
+  const NodeW lf = a.nodes[q];
+  const float3 e = node_ext(lf.meta);
+  // the box centre: lo + ext/2 is a multiple of 2^-22 in [0, 1), exact in FP32
+  const float3 o = make_float3(lf.lo[0] + 0.5f * e.x, lf.lo[1] + 0.5f * e.y, lf.lo[2] + 0.5f * e.z);
+  const int si_o = int(-1 - gw);  // the warp's origin slot (origin64<true>)
+  if (lane == 0) {
+    double* o64 = a.origin64 + 4 * gw;
+    o64[0] = double(o.x);
+    o64[1] = double(o.y);
+    o64[2] = double(o.z);
+  }
+  NodeW* chain = reinterpret_cast<NodeW*>(off + 2 * a.npix + 36);
+  const int leaf = build_chain(a.nodes, o, lane, chain);  // == q
+  const bool soft = (bk.rflags & TREVR2_SOFT) != 0;
+  for (int64_t c0 = p0; c0 < p1; c0 += 32) {
+    const int nrec = int(min(int64_t(32), p1 - c0));
+    int si = 0;
+    float4 xr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float hr = 1.0f;
+    if (lane < nrec) {
+      si = int(bk.keys[c0 + lane]);
+      xr = a.pos32[si];
+      hr = a.hn[si];
+    }
+    double acc[NBP];
+#pragma unroll
+    for (int b = 0; b < NBP; ++b) acc[b] = 0.0;
+    for (int lo = 0;; lo += a.M) {
+      const int total = phase_sources<true>(a, o, si_o, lane, stk, a.stack_ints, U, Up, lo);
+      const int staged = min(total - lo, a.M);
+      make_sources<true>(a, o, si_o, lane, U, Up, staged);
+      const int n = staged > 0 ? bin_sources(a, lane, U, Up, staged, V, off) : 0;
+      if (n > 0) {
+        int* order = off + a.npix;
+        const int nbeams = order_beams(a, lane, V, off, order, order + a.npix);
+        if (lane == 0) *next_beam = 32;
+        __syncwarp();
+        phase_absorb<NBP, true>(a, o, si_o, lane, lstk, V, T, off, order, nbeams, next_beam,
+                                chain, leaf);
+        __syncwarp();
+        eval_bucket<NBP>(a, soft, lane, V, T, n, nrec, xr, hr, acc);
+        __syncwarp();
+      }
+      if (lo + a.M >= total) break;
+    }
+    if (lane < nrec) {
+      float* Jrow = a.J + int64_t(a.order[c0 + lane]) * a.nbsel;
+      for (int c = 0; c < a.nbsel; ++c) {
+        const int b = a.bsel[c];
+        double v = 0.0;
+#pragma unroll
+        for (int d = 0; d < NBP; ++d)
+          if (d == b) v = acc[d];
+        v *= a.inv_size2;
+        if (bk.rflags & TREVR2_THICK) {
+          const double h = double(hr) * a.size;
+          const double tau = double(a.km[int64_t(si) * NBP + b]) / (h * h);
+          if (tau > 0.0) v *= -expm1(-tau) / tau;
+        }
+        Jrow[c] = float(v);
+      }
+    }
+  }
+}
+
+// One warp per bucket; slots from a global counter.
+template <int NBP, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS)
+    k_walk_bucket(WalkArgs a, const __grid_constant__ BucketArgs bk) {
+  extern __shared__ int smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;
+  int* wsm = smem + wib * (a.stack_ints + 2 * a.npix + 36 + 8 * (a.max_depth + 1));
+  int* stk = wsm;
+  int* off = wsm + a.stack_ints;
+  int* next_beam = off + 2 * a.npix + 32;
+  int* lstk = stk + lane * (a.max_depth + 2);
+  SrcEntry* U = a.srcU + gw * a.M;
+  int* Up = a.pixU + gw * a.M;
+  SrcEntry* V = a.srcV + gw * a.M;
+  float* T = a.srcT + gw * a.M * 4;
+  for (;;) {
+    unsigned long long slot = 0;
+    if (lane == 0) slot = atomicAdd(a.counter, 1ull);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (slot >= (unsigned long long)a.A) break;
+    const int64_t p0 = int64_t(slot);
+    const int q = bk.leaf[p0];
+    if (p0 > 0 && bk.leaf[p0 - 1] == q) continue;  // not the first slot of its bucket
+    // the bucket's end: the first later slot in another leaf
+    int64_t p1 = p0 + 1;
+    for (;;) {
+      const int64_t p = p1 + lane;
+      const unsigned same = __ballot_sync(0xffffffffu, p < a.A && bk.leaf[p] == q);
+      if (same == 0xffffffffu) {
+        p1 += 32;
+        continue;
+      }
+      p1 += __ffs(~same) - 1;
+      break;
+    }
+    walk_bucket<NBP>(a, bk, p0, p1, q, gw, lane, stk, off, next_beam, lstk, U, Up, V, T);
   }
 }
 
@@ -526,6 +722,78 @@ static int launch_walk(Tree* t, Table* tb, const int64_t* active, int64_t A, int
   return TREVR2_OK;
 }
 
+template <int NBP>
+static const void* bucket_kernel_nbp() {
+  return reinterpret_cast<const void*>(&k_walk_bucket<NBP, kWalkWarps>);
+}
+
+// TREVR2_BUCKET: receivers in Morton order, the leaf of each, one warp per
+// bucket.
+static int launch_walk_bucket(Tree* t, Table* tb, const int64_t* active, int64_t A, int nside,
+                              float theta, const int* bsel, int nbsel, uint32_t flags, float* J,
+                              cudaStream_t st) {
+  WalkArgs a;
+  // the walk from the bucket centre takes no receiver flags; they go to bk
+  fill_walk_args(t, tb, nside, theta, bsel, nbsel, flags & ~(TREVR2_SOFT | TREVR2_THICK),
+                 kSrcCapacity, &a);
+  a.active = active;
+  a.A = A;
+  a.J = J;
+  const size_t need_order = size_t(A) * (sizeof(uint64_t) + 2 * sizeof(int));
+  if (t->order_bytes < need_order) {
+    if (t->order_buf) cudaFreeAsync(t->order_buf, st);
+    t->order_buf = nullptr;
+    t->order_bytes = 0;
+    cudaError_t e = cudaMallocAsync(&t->order_buf, need_order, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(receiver order)");
+    t->order_bytes = need_order;
+  }
+  uint64_t* keys = static_cast<uint64_t*>(t->order_buf);
+  int* slots = reinterpret_cast<int*>(keys + A);
+  int* leaf = slots + A;
+  const unsigned gb = unsigned((A + 255) / 256);
+  k_order_keys<<<gb, 256, 0, st>>>(active, A, t->N, t->inv, keys, slots);
+  note_launch();
+  if (A > 1) {
+    int bits = 1;
+    while ((int64_t(1) << bits) <= t->N) ++bits;
+    T2_CHECK(radix_sort_u64_i32(keys, slots, A, st, bits));
+  }
+  k_bucket_leaf<<<gb, 256, 0, st>>>(t->child, t->first, keys, A, t->N, leaf);
+  note_launch();
+  a.order = slots;
+  BucketArgs bk;
+  bk.keys = keys;
+  bk.leaf = leaf;
+  bk.rflags = flags & (TREVR2_SOFT | TREVR2_THICK);
+  const void* fn = t->nbp == 1 ? bucket_kernel_nbp<1>()
+                 : t->nbp == 2 ? bucket_kernel_nbp<2>() : bucket_kernel_nbp<4>();
+  const size_t smem = walk_smem(kWalkWarps, a.stack_ints, a.npix, a.max_depth);
+  int per_sm = 0, sms = 0;
+  T2_CHECK(config_walk_kernel(fn, kWalkWarps, smem, &per_sm, &sms));
+  int64_t blocks = int64_t(sms) * per_sm;
+  blocks = std::min<int64_t>(blocks, (A + kWalkWarps - 1) / kWalkWarps);
+  blocks = std::max<int64_t>(blocks, 1);
+  const size_t warps = size_t(blocks) * kWalkWarps;
+  const size_t wb = (walk_buffer_bytes(warps, a.M) + 255) & ~size_t(255);
+  const size_t need = wb + warps * 4 * sizeof(double);
+  if (t->scratch_bytes < need) {
+    if (t->scratch) cudaFreeAsync(t->scratch, st);
+    t->scratch = nullptr;
+    t->scratch_bytes = 0;
+    cudaError_t e = cudaMallocAsync(&t->scratch, need, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(walk buffers)");
+    t->scratch_bytes = need;
+  }
+  place_walk_buffers(static_cast<char*>(t->scratch), warps, a.M, &a.srcU, &a.srcV, &a.srcT, &a.pixU);
+  a.origin64 = reinterpret_cast<double*>(static_cast<char*>(t->scratch) + wb);
+  T2_CUDA(cudaMemsetAsync(t->counter, 0, sizeof(unsigned long long), st));
+  void* args[] = {&a, &bk};
+  T2_CUDA(cudaLaunchKernel(fn, dim3(unsigned(blocks)), dim3(kWalkWarps * 32), args, smem, st));
+  note_launch();
+  return TREVR2_OK;
+}
+
 int read_status(Tree* t, cudaStream_t st) {
   uint32_t s = 0;
   T2_CUDA(cudaMemcpyAsync(&s, t->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -570,7 +838,7 @@ extern "C" int trevr2_J(trevr2_tree* tree, const int64_t* active, int64_t A, int
     set_error("trevr2_J: theta must be positive and finite");
     return TREVR2_EINVAL;
   }
-  if (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_ASYNC)) {
+  if (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_ASYNC | TREVR2_BUCKET)) {
     set_error("trevr2_J: unknown flag bits 0x%x", flags);
     return TREVR2_EINVAL;
   }
@@ -594,7 +862,10 @@ extern "C" int trevr2_J(trevr2_tree* tree, const int64_t* active, int64_t A, int
   if (A == 0) return TREVR2_OK;
   Table* tb = nullptr;
   T2_CHECK(ensure_table(t, nside, st, &tb, (flags & TREVR2_LINEAR) != 0));
-  T2_CHECK(launch_walk(t, tb, active, A, nside, theta, bsel, nbsel, flags, J, st));
+  if (flags & TREVR2_BUCKET)
+    T2_CHECK(launch_walk_bucket(t, tb, active, A, nside, theta, bsel, nbsel, flags, J, st));
+  else
+    T2_CHECK(launch_walk(t, tb, active, A, nside, theta, bsel, nbsel, flags, J, st));
   if (flags & TREVR2_ASYNC) return TREVR2_OK;
   return read_status(t, st);
 }
@@ -719,6 +990,10 @@ extern "C" int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const 
     set_error("trevr2_batch_create: nside %d is not a power of two in [1, %d]", nside,
               TREVR2_MAX_NSIDE);
     return nside > TREVR2_MAX_NSIDE ? TREVR2_EUNSUPPORTED : TREVR2_EINVAL;
+  }
+  if (flags & TREVR2_BUCKET) {
+    set_error("trevr2_batch_create: TREVR2_BUCKET is a trevr2_J flag only");
+    return TREVR2_EUNSUPPORTED;
   }
   if (!(theta > 0.0f) || !std::isfinite(theta) || (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_ASYNC))) {
     set_error("trevr2_batch_create: theta must be positive and finite, flags SOFT|THICK|ASYNC");

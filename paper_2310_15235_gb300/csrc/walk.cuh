@@ -53,6 +53,7 @@ struct WalkArgs {
   int* pixU;
   SrcEntry* srcV;
   float* srcT;      // [warps][M][4] optical depth tau_k(s) of every staged source
+  double* origin64; // [warps][4] FP64 bucket centre of each warp (per-bucket walk)
   int M;
   int stack_ints;   // per warp
   int max_depth;
@@ -192,7 +193,17 @@ __device__ __forceinline__ float3 grazing_coords(const WalkArgs& a, int si, floa
   return make_float3(g[0], g[1], g[2]);
 }
 
-// Sec. 2.5.2: open iff d == 0 or B > theta d.
+// The FP64 origin of a walk: the receiver's FP64 position, or (kBucket) the
+// bucket centre that warp w = -1 - si keeps in origin64[4 w ...].
+template <bool kBucket>
+__device__ __forceinline__ const double* origin64(const WalkArgs& a, int si) {
+  if constexpr (kBucket) return a.origin64 + 4 * int64_t(-1 - si);
+  return a.pos64 + 3 * int64_t(si);
+}
+
+// Sec. 2.5.2: open iff d == 0 or B > theta d, seen from x (receiver si, or
+// with kBucket the centre of the bucket that warp -1 - si walks).
+template <bool kBucket = false>
 __device__ __forceinline__ bool cell_opens(const WalkArgs& a, int q, const NodeW& nd, float3 x,
                                            int si) {
   const float3 e = node_ext(nd.meta);
@@ -205,8 +216,7 @@ __device__ __forceinline__ bool cell_opens(const WalkArgs& a, int q, const NodeW
   const float margin = B * B - a.theta2 * d2;
   const float g = 2.2f * B * (a.guard_abs + a.guard_rel * B);
   if (fabsf(margin) > g) return margin > 0.0f;
-  return opens64(a.pos64 + 3 * int64_t(si), a.B64[q], a.theta64, nd.lo[0], nd.lo[1], nd.lo[2],
-                 nd.meta);
+  return opens64(origin64<kBucket>(a, si), a.B64[q], a.theta64, nd.lo[0], nd.lo[1], nd.lo[2], nd.meta);
 }
 
 // Eq. intint as a kernel of r for an element of size h (normalised units).
@@ -234,7 +244,10 @@ static __device__ float soft_kernel(float r, float h) {
 }
 
 // Bin one source: beam, projected distance, r/s, kernel.  Returns false for
-// a source on top of the receiver (r == 0) or with s <= 0.
+// a source on top of the receiver (r == 0) or with s <= 0.  From a bucket
+// centre (kBucket) r/s is the centre's and goes unused and there is no
+// kernel: each receiver of the bucket applies its own distance.
+template <bool kBucket = false>
 __device__ __forceinline__ bool make_source(const WalkArgs& a, float3 p, const double* p64,
                                             float3 x, int si, int ref, SrcEntry& out, int& pix) {
   const float vx = p.x - x.x, vy = p.y - x.y, vz = p.z - x.z;
@@ -243,7 +256,7 @@ __device__ __forceinline__ bool make_source(const WalkArgs& a, float3 p, const d
   const float r = sqrtf(r2);
   int k = hp_vec2pix_f32(a.nside, vx, vy, vz, hp_guard(a.nside, r));
   if (k < 0) {
-    const double* x64 = a.pos64 + 3 * int64_t(si);
+    const double* x64 = origin64<kBucket>(a, si);
     k = hp_vec2pix_f64(a.nside, __dsub_rn(p64[0], x64[0]), __dsub_rn(p64[1], x64[1]),
                        __dsub_rn(p64[2], x64[2]));
   }
@@ -252,7 +265,8 @@ __device__ __forceinline__ bool make_source(const WalkArgs& a, float3 p, const d
   if (!(s > 0.0f)) return false;
   out.s = s;
   out.rs = r / s;
-  out.w = (a.flags & TREVR2_SOFT) ? soft_kernel(r, a.hn[si]) : 1.0f / (kFourPi * r2);
+  if constexpr (kBucket) out.w = 0.0f;
+  else out.w = (a.flags & TREVR2_SOFT) ? soft_kernel(r, a.hn[si]) : 1.0f / (kFourPi * r2);
   out.ref = ref;
   pix = k;
   return true;
@@ -271,6 +285,7 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 // references (a cell index, or an element index with kRefElement) go to
 // U[].ref; make_sources then fills the records.  Returns the total number of
 // sources of this receiver (warp-uniform).
+template <bool kBucket = false>
 static __device__ int phase_sources(const WalkArgs& a, float3 x, int si, int lane, int* stk, int cap,
                              SrcEntry* U, int* Up, int lo) {
   int sp = 1;
@@ -288,7 +303,7 @@ static __device__ int phase_sources(const WalkArgs& a, float3 x, int si, int lan
     if (q >= 0) {
       const NodeW nd = a.nodes[q];
       if (nd.meta & kMetaHasL) {
-        if (!cell_opens(a, q, nd, x, si)) {
+        if (!cell_opens<kBucket>(a, q, nd, x, si)) {
           emit_node = true;
         } else if (nd.meta & kMetaLeaf) {
           leaf_first = nd.aux;
@@ -340,6 +355,7 @@ static __device__ int phase_sources(const WalkArgs& a, float3 x, int si, int lan
 // The records of the n staged sources, all lanes at once: beam, projected
 // distance, r/s, kernel (make_source); a source the method skips (r = 0, or
 // not in front of its beam) gets beam -1.
+template <bool kBucket = false>
 static __device__ void make_sources(const WalkArgs& a, float3 x, int si, int lane, SrcEntry* U,
                                     int* Up, int n) {
   for (int e = lane; e < n; e += 32) {
@@ -358,7 +374,7 @@ static __device__ void make_sources(const WalkArgs& a, float3 x, int si, int lan
     }
     SrcEntry ent;
     int pix = -1;
-    if (make_source(a, p, p64, x, si, ref, ent, pix)) U[e] = ent; else pix = -1;
+    if (make_source<kBucket>(a, p, p64, x, si, ref, ent, pix)) U[e] = ent; else pix = -1;
     Up[e] = pix;
   }
   __syncwarp();
