@@ -315,6 +315,18 @@ def run_ours(args, world, rank, local):
         rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
         extra["parity_sample"] = {"receivers": 512, "median_rel": float(np.median(rel)),
                                   "max_rel": float(rel.max())}
+        if not args.no_bucket:
+            extra["bucket"] = run_bucket(case, inp, dev, walk_avg)
+            ref = ot.J(sample[:256], case["nside"], case["theta"], flags=t2.BUCKET,
+                       nthreads=cores)
+            got = extra["bucket"].pop("_J")[sample[:256]]
+            rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
+            extra["bucket"]["parity_sample"] = {"receivers": 256,
+                                                "median_rel": float(np.median(rel)),
+                                                "max_rel": float(rel.max())}
+    elif world == 1 and not args.no_bucket:
+        extra["bucket"] = run_bucket(case, inp, dev, walk_avg)
+        extra["bucket"].pop("_J")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -491,6 +503,38 @@ def run_adjoint(args, dev):
             "backward_units_per_s": units / (bwd * 1e-3)}
 
 
+def run_bucket(case, inp, dev, per_receiver_walk_ms, reps=3):
+    """Per-bucket beams (TREVR2_BUCKET) on the benchmark field: the same J
+    with one walk per leaf from its centre; tree and tables built once, one
+    warm-up and `reps` timed walks."""
+    import torch
+
+    import paper_2310_15235_gb300 as t2
+
+    tree = t2.build(inp["pos"], inp["mass"], inp["kappa"], inp["lum"], inp["h"], case["box_lo"],
+                    case["box_size"], case["bucket"], device=dev)
+    tree.prepare(case["nside"])
+    A, nb, npix = len(case["active"]), case["nb"], 12 * case["nside"] ** 2
+    J = torch.empty((A, nb), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    flags = t2.ASYNC | t2.BUCKET
+    tree.J(inp["active"], case["nside"], case["theta"], out=J, flags=flags)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        tree.J(inp["active"], case["nside"], case["theta"], out=J, flags=flags)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tree.status()
+    ms = e0.elapsed_time(e1) / reps
+    out = {"walk_ms": ms, "units_per_s": A * npix * nb / (ms * 1e-3), "unit": UNIT,
+           "kernel": "k_walk_bucket", "speedup_vs_per_receiver": per_receiver_walk_ms / ms,
+           "_J": J.cpu().numpy()}
+    tree.free()
+    return out
+
+
 def run_adjoint_clumpy(case, inp, dev):
     """Adjoint / forward on the benchmark field itself (2,097,152 receivers,
     nside 4, 3 bands), Loss = sum w J with w ~ U(0,1); one warm-up and two
@@ -548,14 +592,16 @@ def run_walk_only(args):
     for k in range(args.warmup + args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        tree.J(inp["active"], case["nside"], case["theta"], out=J, flags=t2.ASYNC)
+        tree.J(inp["active"], case["nside"], case["theta"], out=J,
+               flags=t2.ASYNC | (t2.BUCKET if args.bucket else 0))
         e1.record()
         torch.cuda.synchronize()
         if k >= args.warmup:
             times.append(e0.elapsed_time(e1))
     tree.status()
     ms = float(np.mean(times))
-    print(json.dumps({"mode": "walk-only", "lattice": n, "receivers": A, "walk_ms": ms,
+    print(json.dumps({"mode": "walk-only", "bucket": bool(args.bucket), "lattice": n,
+                      "receivers": A, "walk_ms": ms,
                       "units_per_s": A * npix * nb / (ms * 1e-3), "nodes": tree.n_nodes,
                       "max_depth": tree.max_depth}), flush=True)
     tree.free()
@@ -573,6 +619,10 @@ def main():
     ap.add_argument("--walk-only", action="store_true",
                     help="time only the walk kernel on a lattice^3 clumpy field (profiling)")
     ap.add_argument("--lattice", type=int, default=128)
+    ap.add_argument("--bucket", action="store_true",
+                    help="with --walk-only: per-bucket beams (TREVR2_BUCKET)")
+    ap.add_argument("--no-bucket", action="store_true",
+                    help="skip the per-bucket beams measurement")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the individual-timestep batching measurement")
     ap.add_argument("--batched-reps", type=int, default=2)

@@ -7,9 +7,10 @@ clouds, a source beside a wall) are checked three ways:
     and against 1-D quadratures of each geometry written out here;
   * the exact figures of merit against the "Exact" rows of Table escape,
     which fixes the reading of each geometry from the text;
-  * the oracle's TREVR2 (transmission and linear averaging) against the
-    table's TREVR2 rows.  Those rows come from a glass and per-bucket rays;
-    here a jittered lattice and per-receiver rays stand in, so the bands are
+  * the oracle's TREVR2 (transmission and linear averaging, with
+    per-receiver and with per-bucket beams) against the table's TREVR2 rows.
+    Those rows come from a glass; here a jittered lattice stands in, so the
+    bands are
     those that separate the table's methods from one another (a few tenths
     of a percent of escape on the one-source tests), not rounding.
 """
@@ -24,6 +25,7 @@ import workloads
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 LINEAR = 8
+BUCKET = 16
 
 
 def _table():
@@ -173,23 +175,27 @@ def oracle_figures(oracle_mod, esc):
         ot = oracle_mod.OracleTree.from_case(case)
         pts = case["pos"][case["active"]]
         for method, flags in (("transmission", 0), ("linear", LINEAR)):
-            J = ot.J(case["active"], case["nside"], case["theta"], flags=flags)[:, 0]
-            out[(name, method)] = esc.figures(J, pts, case["geometry"])
+            for walk, wflag in (("receiver", 0), ("bucket", BUCKET)):
+                J = ot.J(case["active"], case["nside"], case["theta"], flags=flags | wflag)[:, 0]
+                out[(name, method, walk)] = esc.figures(J, pts, case["geometry"])
     return out
 
 
+@pytest.mark.parametrize("walk", ["receiver", "bucket"])
 @pytest.mark.parametrize("key", sorted(BANDS))
-def test_oracle_matches_table_rows(oracle_figures, key):
-    e, c = oracle_figures[key]
+def test_oracle_matches_table_rows(oracle_figures, key, walk):
+    """Per-receiver beams and the paper's own per-bucket beams alike."""
+    e, c = oracle_figures[key + (walk,)]
     want = _table()[key]
     de, dc = BANDS[key]
     assert abs(e - want[0]) <= de and abs(c - want[1]) <= dc, (key, e, c, want)
 
 
-def test_linear_average_fails_on_the_combined_cloud(oracle_figures):
+@pytest.mark.parametrize("walk", ["receiver", "bucket"])
+def test_linear_average_fails_on_the_combined_cloud(oracle_figures, walk):
     """Sec. 3.3: once the sources and the dense cloud share a cell the
     linear average wipes out most of the flux at r = 6 (the table prints
     33.7 %, covering 0.684), while the transmission average keeps it."""
-    e_l, c_l = oracle_figures[("two_sources_cloud", "linear")]
-    e_t, _ = oracle_figures[("two_sources_cloud", "transmission")]
+    e_l, c_l = oracle_figures[("two_sources_cloud", "linear", walk)]
+    e_t, _ = oracle_figures[("two_sources_cloud", "transmission", walk)]
     assert e_l < 0.5 and c_l > 0.5 and e_t - e_l > 0.4, (e_l, c_l, e_t)
