@@ -33,6 +33,7 @@ FLAG_SOFT = 1
 FLAG_THICK = 2
 FLAG_LINEAR = 8
 FLAG_BUCKET = 16
+FLAG_PP = 32
 
 
 def build(force: bool = False) -> str:
@@ -86,6 +87,8 @@ def _load():
         lib.oracle_cell_opens.argtypes = [P, P, P, P, f64, P]
         lib.oracle_beam_tau.restype = f64
         lib.oracle_beam_tau.argtypes = [P, i64, i32, f64, i64, f64, i32]
+        lib.oracle_pp_sphere.restype = i64
+        lib.oracle_pp_sphere.argtypes = [P, i64, i32, P, P]
         _lib = lib
         return lib
 
@@ -239,6 +242,17 @@ class OracleTree:
         """Optical depth along beam k of receiver i up to distance s (no r/s)."""
         return _load().oracle_beam_tau(self._h, int(i), int(nside), float(theta), int(k),
                                        float(s), int(band))
+
+    def pp_sphere(self, i, nside):
+        """(r_pp, sorted original indices of the p-p particles) of the bucket
+        that holds element i (FLAG_PP)."""
+        rpp = np.zeros(1)
+        n = _load().oracle_pp_sphere(self._h, int(i), int(nside), _p(rpp), None)
+        if n < 0:
+            raise ValueError("bad element or nside")
+        out = np.empty(n, np.int64)
+        _load().oracle_pp_sphere(self._h, int(i), int(nside), _p(rpp), _p(out))
+        return float(rpp[0]), out
 
     def J_deriv(self, active, nside, theta, which, elem, band, flags=0, nthreads=0):
         """dJ[A][nb]/d(kappa or lum)[elem][band] by forward-mode duals."""

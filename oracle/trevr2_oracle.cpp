@@ -50,6 +50,18 @@
 //     depth up to s is multiplied by r/s with r the receiver's own distance
 //     to the source, and the kernel is g(r).  A source at the bucket centre
 //     itself has no beam and is skipped, as one on top of a receiver is.
+//  R11 FLAG_PP (with FLAG_BUCKET; Sec. 2.4, Sec. 2.5): the p-p radius r_pp of
+//     a bucket starts at the radius of the sphere through its box corners and
+//     grows to h_j / sqrt(4 pi / N_ray) for the largest gas element j (m > 0)
+//     within r_pp of the bucket centre, until no element inside is larger
+//     than the beam width r_pp sqrt(4 pi / N_ray) there.  Those elements are
+//     the bucket's p-p particles.  Cells whose box comes within r_pp of the
+//     centre open (sources there are single elements), beams count cell
+//     absorption only beyond r_pp, and per receiver and source every p-p
+//     particle j (not the receiver, not the source) that is closer to the
+//     source than the receiver is and lies within h_j of the receiver-source
+//     segment (distance b) adds kappa_j Sigma_j(b), Sigma_j(b) =
+//     3 m_j / (pi h_j^2) (1 - b / h_j), whose area integral over b < h_j is m_j.
 
 #include <algorithm>
 #include <atomic>
@@ -549,7 +561,8 @@ bool ray_chord(const double x[3], const double n[3], const double blo[3], const 
   return t1 > t0;
 }
 
-enum : uint32_t { FLAG_SOFT = 1u, FLAG_THICK = 2u, FLAG_LINEAR = 8u, FLAG_BUCKET = 16u };
+enum : uint32_t { FLAG_SOFT = 1u, FLAG_THICK = 2u, FLAG_LINEAR = 8u, FLAG_BUCKET = 16u,
+                  FLAG_PP = 32u };
 
 struct WalkStats {
   int64_t visited = 0;   // nodes given the opening test
@@ -573,7 +586,39 @@ struct Problem {
   std::vector<double> dirs;   // [npix][3]
   std::vector<int64_t> pair;  // [npix]
   std::vector<int64_t> leaf_of;  // [N] original index -> its leaf (FLAG_BUCKET)
+  std::vector<double> pp_r;                  // [nodes] r_pp of each leaf (FLAG_PP)
+  std::vector<std::vector<int64_t>> pp_list; // [nodes] its p-p particles (original)
 };
+
+// R11: the p-p radius and particles of the bucket centred on xo whose box
+// reaches r0 from its centre, by scanning every element.
+inline double element_h(const Tree& t, int64_t j, double h_default) {
+  return t.h.empty() ? h_default : t.h[j];
+}
+
+void pp_sphere(const Tree& t, const double xo[3], double r0, double beam, double h_default,
+               double& rpp, std::vector<int64_t>& list) {
+  auto dist = [&](int64_t j) {
+    double s = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      const double d = t.pos[3 * j + a] - xo[a];
+      s += d * d;
+    }
+    return std::sqrt(s);
+  };
+  rpp = r0;
+  for (int it = 0; it < 64; ++it) {
+    double H = 0.0;
+    for (int64_t j = 0; j < t.N; ++j)
+      if (t.mass[j] > 0.0 && dist(j) < rpp) H = std::max(H, element_h(t, j, h_default));
+    const double grown = std::max(rpp, H / beam);
+    if (grown == rpp) break;
+    rpp = grown;
+  }
+  list.clear();
+  for (int64_t j = 0; j < t.N; ++j)
+    if (t.mass[j] > 0.0 && dist(j) < rpp) list.push_back(j);
+}
 
 // J of one receiver, every band (Sec. 2.5).
 template <class T>
@@ -592,13 +637,18 @@ void walk_receiver(const Problem<T>& pr, int64_t i_orig, T* Jout, WalkStats* st)
     node_box(t.nodes[pr.leaf_of[i_orig]], t.lo, t.size, blo, bhi);
     for (int a = 0; a < 3; ++a) xo[a] = 0.5 * (blo[a] + bhi[a]);
   }
+  // R11: the bucket's p-p radius and particles
+  const bool pp = (pr.flags & FLAG_PP) != 0;
+  const double rpp = pp ? pr.pp_r[pr.leaf_of[i_orig]] : 0.0;
+  const std::vector<int64_t>* pplist = pp ? &pr.pp_list[pr.leaf_of[i_orig]] : nullptr;
   struct CutCell {
     int64_t node;
     double lo[3], hi[3];
   };
   struct Src {
     T p[3];
-    const T* L;  // nb luminosities
+    const T* L;         // nb luminosities
+    int64_t elem = -1;  // the element, for a single-element source
   };
   std::vector<CutCell> cut;
   std::vector<Src> srcs;
@@ -619,7 +669,8 @@ void walk_receiver(const Problem<T>& pr, int64_t i_orig, T* Jout, WalkStats* st)
     cc.node = q;
     node_box(nd, t.lo, t.size, cc.lo, cc.hi);
     ++ws.visited;
-    bool open = cell_opens(xo, cc.lo, cc.hi, ag.B[q], pr.theta);
+    bool open = cell_opens(xo, cc.lo, cc.hi, ag.B[q], pr.theta) ||
+                (pp && box_distance(xo, cc.lo, cc.hi) < rpp);
     if (!open) {
       cut.push_back(cc);
       if (val(ag.Ltot[q]) > 0.0) {
@@ -639,6 +690,7 @@ void walk_receiver(const Problem<T>& pr, int64_t i_orig, T* Jout, WalkStats* st)
         Src s;
         for (int a = 0; a < 3; ++a) s.p[a] = T(t.pos[3 * j + a]);
         s.L = &(*pr.lum)[j * nb];
+        s.elem = j;
         srcs.push_back(s);
       }
     } else {
@@ -659,6 +711,10 @@ void walk_receiver(const Problem<T>& pr, int64_t i_orig, T* Jout, WalkStats* st)
     for (const CutCell& cc : cut) {
       double t0, t1;
       if (!ray_chord(xo, nk, cc.lo, cc.hi, t0, t1)) continue;
+      if (pp) {  // R11: cells absorb only beyond r_pp
+        t0 = std::max(t0, rpp);
+        if (!(t1 > t0)) continue;
+      }
       segs[k].push_back({t0, t1, &(*pr.tab)[(cc.node * P + pr.pair[k]) * nb]});
       ++ws.segments;
     }
@@ -683,6 +739,28 @@ void walk_receiver(const Problem<T>& pr, int64_t i_orig, T* Jout, WalkStats* st)
     if (val(r) == 0.0) continue;
     ++ws.sources;
     T g = (pr.flags & FLAG_SOFT) ? soft_kernel(r, hi_) : T(1.0) / (4.0 * kPi * r * r);
+    // R11: the p-p particles in front of the receiver that cross the segment
+    std::vector<T> taupp(nb, T(0.0));
+    if (pp) {
+      for (int64_t j : *pplist) {
+        if (j == i_orig || j == s.elem) continue;
+        const double* xj = &t.pos[3 * j];
+        T dj[3] = {xj[0] - s.p[0], xj[1] - s.p[1], xj[2] - s.p[2]};
+        T djs = sqrt(dj[0] * dj[0] + dj[1] * dj[1] + dj[2] * dj[2]);
+        if (!(val(djs) < val(r))) continue;  // not closer to the source
+        // distance from x_j to the segment x_i -> source
+        T w[3] = {xj[0] - xi[0], xj[1] - xi[1], xj[2] - xi[2]};
+        T tt = (w[0] * v[0] + w[1] * v[1] + w[2] * v[2]) / (r * r);
+        if (val(tt) < 0.0) tt = T(0.0);
+        if (val(tt) > 1.0) tt = T(1.0);
+        T e[3] = {w[0] - tt * v[0], w[1] - tt * v[1], w[2] - tt * v[2]};
+        T bj = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+        const double hj = element_h(t, j, pr.h_default);
+        if (!(val(bj) < hj)) continue;
+        T sigma = (3.0 * t.mass[j] / (kPi * hj * hj)) * (T(1.0) - bj / hj);
+        for (int b = 0; b < nb; ++b) taupp[b] += (*pr.kappa)[j * nb + b] * sigma;
+      }
+    }
     for (int b = 0; b < nb; ++b) {
       T tau = 0.0;
       for (const Seg& sg : segs[k]) {
@@ -690,7 +768,7 @@ void walk_receiver(const Problem<T>& pr, int64_t i_orig, T* Jout, WalkStats* st)
         T len = (val(sp) < sg.t1) ? (sp - sg.t0) : T(sg.t1 - sg.t0);
         tau += sg.alpha[b] * len;
       }
-      tau = tau * (r / sp);
+      tau = tau * (r / sp) + taupp[b];
       Jout[b] += s.L[b] * exp(-tau) * g;
     }
   }
@@ -728,7 +806,7 @@ Problem<T> make_problem(const Tree& t, const Aggregates<T>& ag, const std::vecto
     pix2vec_ring(nside, k, &pr.dirs[3 * k]);
     pr.pair[k] = pair_of_pixel(nside, k);
   }
-  if (flags & FLAG_BUCKET) {
+  if (flags & (FLAG_BUCKET | FLAG_PP)) {
     pr.leaf_of.assign(t.N, -1);
     for (size_t q = 0; q < t.nodes.size(); ++q) {
       const Node& nd = t.nodes[q];
@@ -758,6 +836,36 @@ void parallel_for(int64_t n, int nthreads, F&& f) {
       }
     });
   for (auto& th : pool) th.join();
+}
+
+// R11: r_pp and the p-p particles of every bucket that holds a receiver.
+template <class T>
+void prepare_pp(Problem<T>& pr, const int64_t* active, int64_t A, int nthreads) {
+  if (!(pr.flags & FLAG_PP)) return;
+  const Tree& t = *pr.t;
+  pr.pp_r.assign(t.nodes.size(), 0.0);
+  pr.pp_list.assign(t.nodes.size(), {});
+  std::vector<char> seen(t.nodes.size(), 0);
+  std::vector<int64_t> leaves;
+  for (int64_t a = 0; a < A; ++a) {
+    const int64_t q = pr.leaf_of[active[a]];
+    if (!seen[q]) {
+      seen[q] = 1;
+      leaves.push_back(q);
+    }
+  }
+  const int64_t npix = 12 * static_cast<int64_t>(pr.nside) * pr.nside;
+  const double beam = std::sqrt(4.0 * kPi / static_cast<double>(npix));
+  parallel_for(static_cast<int64_t>(leaves.size()), nthreads, [&](int64_t l) {
+    const int64_t q = leaves[l];
+    double blo[3], bhi[3], xo[3], r0 = 0.0;
+    node_box(t.nodes[q], t.lo, t.size, blo, bhi);
+    for (int a = 0; a < 3; ++a) {
+      xo[a] = 0.5 * (blo[a] + bhi[a]);
+      r0 += 0.25 * (bhi[a] - blo[a]) * (bhi[a] - blo[a]);
+    }
+    pp_sphere(t, xo, std::sqrt(r0), beam, pr.h_default, pr.pp_r[q], pr.pp_list[q]);
+  });
 }
 
 struct OracleTree {
@@ -923,12 +1031,14 @@ double oracle_thick_factor(double tau) { return thick_factor<double>(tau); }
 int oracle_J(void* h, const int64_t* active, int64_t A, int nside, double theta, uint32_t flags,
              double* J, int nthreads, int64_t* stats) {
   if (!valid_nside(nside) || !(theta > 0.0)) return -1;
+  if ((flags & FLAG_PP) && !(flags & FLAG_BUCKET)) return -1;
   OracleTree& ot = *static_cast<OracleTree*>(h);
   for (int64_t a = 0; a < A; ++a)
     if (active[a] < 0 || active[a] >= ot.t.N) return -1;
   ensure_table(ot, nside, (flags & FLAG_LINEAR) != 0);
   Problem<double> pr = make_problem<double>(ot.t, ot.ag, ot.tab, ot.t.kappa, ot.t.lum, nside,
                                             theta, flags);
+  prepare_pp(pr, active, A, nthreads);
   const int nb = ot.t.nb;
   parallel_for(A, nthreads, [&](int64_t a) {
     WalkStats ws;
@@ -949,6 +1059,7 @@ int oracle_J(void* h, const int64_t* active, int64_t A, int nside, double theta,
 int oracle_J_deriv(void* h, const int64_t* active, int64_t A, int nside, double theta,
                    uint32_t flags, int which, int64_t elem, int band, double* dJ, int nthreads) {
   if (!valid_nside(nside) || !(theta > 0.0)) return -1;
+  if ((flags & FLAG_PP) && !(flags & FLAG_BUCKET)) return -1;
   OracleTree& ot = *static_cast<OracleTree*>(h);
   const Tree& t = ot.t;
   const int nb = t.nb;
@@ -960,12 +1071,31 @@ int oracle_J_deriv(void* h, const int64_t* active, int64_t A, int nside, double 
   Aggregates<Dual> ag = compute_aggregates<Dual>(t, kappa, lum);
   std::vector<Dual> tab = alpha_tables<Dual>(t, ag, nside, (flags & FLAG_LINEAR) != 0);
   Problem<Dual> pr = make_problem<Dual>(t, ag, tab, kappa, lum, nside, theta, flags);
+  prepare_pp(pr, active, A, nthreads);
   parallel_for(A, nthreads, [&](int64_t a) {
     std::vector<Dual> Jd(nb);
     walk_receiver<Dual>(pr, active[a], Jd.data(), nullptr);
     for (int b = 0; b < nb; ++b) dJ[a * nb + b] = Jd[b].d;
   });
   return 0;
+}
+
+// R11: r_pp and the p-p particles (original indices, sorted) of the leaf
+// holding element i for this nside; list may be NULL (count only).
+// Returns the number of particles, or -1.
+int64_t oracle_pp_sphere(void* h, int64_t i, int nside, double* rpp, int64_t* list) {
+  OracleTree& ot = *static_cast<OracleTree*>(h);
+  const Tree& t = ot.t;
+  if (i < 0 || i >= t.N || !valid_nside(nside)) return -1;
+  Problem<double> pr = make_problem<double>(t, ot.ag, ot.tab, t.kappa, t.lum, nside, 1.0,
+                                            FLAG_BUCKET | FLAG_PP);
+  prepare_pp(pr, &i, 1, 1);
+  const int64_t q = pr.leaf_of[i];
+  *rpp = pr.pp_r[q];
+  std::vector<int64_t> l = pr.pp_list[q];
+  std::sort(l.begin(), l.end());
+  if (list) std::copy(l.begin(), l.end(), list);
+  return static_cast<int64_t>(l.size());
 }
 
 // Opening decision for one cell with the given centre of luminosity.

@@ -760,3 +760,115 @@ def test_bucket_receivers_share_the_beam(oracle_mod):
         shared.append(np.array(spread))
     assert np.all(shared[0] <= 1e-9 * 40.0)
     assert shared[1].max() > 1e-3
+
+
+# ----------------------------------------------------------------------------
+# Particle-particle absorption inside r_pp (Sec. 2.4, flags BUCKET | PP)
+
+def _pp_case(absorber_pos, h_abs=0.1, m_abs=0.002, kappa_abs=(30.0, 7.0)):
+    """Receiver gas element at (0.3, 0.5, 0.5), an L = 1 star at (0.7, 0.5,
+    0.5) and one absorber, all in the root leaf of [0, 1)^3 (bucket 12): the
+    bucket centre is the box centre and r_pp >= sqrt(3)/2 holds everything,
+    so the star is inside r_pp and J is the p-p attenuation alone."""
+    pos = np.array([[0.3, 0.5, 0.5], [0.7, 0.5, 0.5], absorber_pos], dtype=np.float64)
+    mass = np.array([1e-3, 0.0, m_abs])
+    kappa = np.array([[0.0, 0.0], [0.0, 0.0], list(kappa_abs)])
+    lum = np.array([[0.0, 0.0], [1.0, 1.0], [0.0, 0.0]])
+    h = np.array([0.05, 0.05, h_abs])
+    case = workloads._pack("pp", pos, mass, kappa, lum, h, np.array([0]), 2, 0.75, bucket=12)
+    return case
+
+
+def test_pp_single_absorber_closed_form(oracle_mod):
+    """J = L e^{-kappa 3 m (1 - b/h) / (pi h^2)} / (4 pi r^2) for an absorber
+    whose centre is at distance b < h from the receiver-source segment, and
+    no attenuation for b >= h or for an absorber behind the receiver."""
+    flags = oracle_mod.FLAG_BUCKET | oracle_mod.FLAG_PP
+    J0 = 1.0 / (4 * np.pi * 0.4 ** 2)
+    h, m, kap = 0.1, 0.002, np.array([30.0, 7.0])
+    for b in (0.0, 0.013, 0.05, 0.0999, 0.1, 0.17):
+        case = _pp_case([0.5, 0.5 + b, 0.5])
+        # the inputs are FP32: use the stored values
+        h, m = float(case["h"][2]), float(case["mass"][2])
+        kap = case["kappa"][2].astype(np.float64)
+        t = oracle_mod.OracleTree.from_case(case)
+        rpp, members = t.pp_sphere(0, 2)
+        assert rpp >= math.sqrt(3) / 2 and list(members) == [0, 2]
+        J = t.J([0], 2, 0.75, flags=flags)[0]
+        tau = kap * 3 * m / (math.pi * h * h) * max(0.0, 1 - b / h)
+        np.testing.assert_allclose(J, J0 * np.exp(-tau), rtol=1e-13)
+    for behind in ([0.2, 0.5, 0.5], [0.25, 0.52, 0.5]):
+        t = oracle_mod.OracleTree.from_case(_pp_case(behind))
+        np.testing.assert_allclose(t.J([0], 2, 0.75, flags=flags)[0], J0, rtol=1e-13)
+
+
+def test_pp_column_integrates_to_the_mass(oracle_mod):
+    """The p-p column seen at impact parameter b, recovered from J, integrates
+    over the disc b < h to the absorber's kappa m (Sec. 2.4's normalisation),
+    by quadrature over b."""
+    flags = oracle_mod.FLAG_BUCKET | oracle_mod.FLAG_PP
+    J0 = 1.0 / (4 * np.pi * 0.4 ** 2)
+    h, m, kap = 0.1, 0.002, np.array([30.0, 7.0])
+    bs = (np.arange(64) + 0.5) / 64 * h  # midpoint rule on [0, h)
+    tau = []
+    for b in bs:
+        case = _pp_case([0.5, 0.5, 0.5 + b], h, m, kap)
+        t = oracle_mod.OracleTree.from_case(case)
+        tau.append(-np.log(t.J([0], 2, 0.75, flags=flags)[0] / J0))
+    tau = np.array(tau)
+    hf, mf = float(case["h"][2]), float(case["mass"][2])  # the FP32 inputs
+    kf = case["kappa"][2].astype(np.float64)
+    integral = (tau * 2 * np.pi * bs[:, None]).sum(0) * (h / 64)
+    # midpoint rule on [0, 0.1) while the column ends at the FP32 h
+    np.testing.assert_allclose(integral, kf * mf, rtol=2e-4)
+
+
+def test_pp_radius_brute_force(oracle_mod):
+    """r_pp by its definition: from the radius of the sphere through the
+    bucket's corners, grown to h_j / sqrt(4 pi / N_ray) for the largest gas
+    element inside until nothing inside is larger than the beam."""
+    case = workloads.random_case(700, 20, nb=1, seed=121, clumped=True)
+    rng = np.random.default_rng(3)
+    case["h"] = (case["h"] * rng.uniform(0.3, 3.0, len(case["h"]))).astype(np.float32)
+    t = oracle_mod.OracleTree.from_case(case)
+    e = t.export()
+    pos, h, mass = case["pos"], case["h"].astype(np.float64), case["mass"]
+    gas = mass > 0
+    leaf_of = np.empty(len(pos), np.int64)
+    for q in np.flatnonzero(e["child"] < 0):
+        leaf_of[e["perm"][e["first"][q]: e["first"][q] + e["count"][q]]] = q
+    for nside in (1, 2, 4):
+        beam = math.sqrt(4 * math.pi / (12 * nside * nside))
+        for i in rng.choice(np.flatnonzero(gas), 25, replace=False):
+            box = e["box"][leaf_of[i]]
+            c = 0.5 * (box[:3] + box[3:])
+            r = 0.5 * np.linalg.norm(box[3:] - box[:3])
+            d = np.linalg.norm(pos - c, axis=1)
+            while True:
+                inside = gas & (d < r)
+                grown = max(r, h[inside].max() / beam) if inside.any() else r
+                if grown == r:
+                    break
+                r = grown
+            rpp, members = t.pp_sphere(int(i), nside)
+            assert rpp == pytest.approx(r, rel=1e-14)
+            np.testing.assert_array_equal(members, np.flatnonzero(gas & (d < r)))
+
+
+@pytest.mark.parametrize("n_gas,n_src,nb,seed,bucket", [(150, 9, 2, 1, 12), (300, 12, 1, 5, 4)])
+def test_pp_brute_force_theta0_without_absorption(oracle_mod, n_gas, n_src, nb, seed, bucket):
+    """kappa = 0: p-p particles absorb nothing, and theta -> 0 opens every
+    cell, so J is the direct sum at every receiver's own distance."""
+    case = workloads.random_case(n_gas, n_src, nb=nb, seed=seed, clumped=True, bucket=bucket,
+                                 n_active=(n_gas + n_src) // 2)
+    case["kappa"][:] = 0.0
+    t = oracle_mod.OracleTree.from_case(case)
+    J = t.J(case["active"], 2, 1e-9, flags=oracle_mod.FLAG_BUCKET | oracle_mod.FLAG_PP)
+    np.testing.assert_allclose(J, _brute_J(case), rtol=1e-11, atol=1e-300)
+
+
+def test_pp_needs_bucket(oracle_mod):
+    case = workloads.random_case(100, 5, seed=122)
+    t = oracle_mod.OracleTree.from_case(case)
+    with pytest.raises(ValueError):
+        t.J(case["active"], 2, 0.75, flags=oracle_mod.FLAG_PP)
