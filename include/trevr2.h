@@ -56,6 +56,8 @@ extern "C" {
                              leaf holding receivers, from its box centre; each
                              receiver scales the beam optical depth by its own
                              distance over the projected one (trevr2_J only) */
+#define TREVR2_PP 32u    /* with TREVR2_BUCKET: particle-particle absorption inside
+                            the bucket's p-p radius (Sec. 2.4; trevr2_J only) */
 
 /* Supported sizes: 1 <= nb <= 4 bands; nside a power of two in [1, 16];
  * N < 2^31 elements; 1 <= bucket <= 4096. */
@@ -106,15 +108,24 @@ int trevr2_build(const double* pos, const float* mass, const float* kappa, const
  *  theta   opening parameter theta_rad > 0 (paper default 0.75)
  *  bands   host [nbsel] band indices to return, or NULL = all nb bands
  *  flags   TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_BUCKET |
- *          TREVR2_ASYNC.  With TREVR2_BUCKET the cut, the beam of each source,
+ *          TREVR2_PP | TREVR2_ASYNC.  With TREVR2_BUCKET the cut, the beam of each source,
  *          its projected distance s and the optical depth to s are those of
  *          the centre of the leaf box holding the receiver, shared by every
  *          receiver of that leaf; each receiver adds L g(r) e^{-tau r/s} with
  *          r its own distance to the source (its own h and Eq. taucorr
  *          factor under TREVR2_SOFT / TREVR2_THICK).  A source exactly at a
- *          bucket centre has no beam and is skipped.  trevr2_J_backward,
- *          the batches and trevr2_J_noalloc do not take this flag
- *          (EUNSUPPORTED, EUNSUPPORTED, EINVAL).
+ *          bucket centre has no beam and is skipped.  TREVR2_PP (needs
+ *          TREVR2_BUCKET, else EINVAL) adds Sec. 2.4: the bucket's p-p radius
+ *          r_pp starts at the sphere through its box corners and grows until
+ *          no gas element (m > 0) inside is wider than the beam there
+ *          (h <= r_pp sqrt(4 pi / N_ray)); cells within r_pp open, cell
+ *          absorption counts beyond r_pp only, and every p-p particle k
+ *          (not the receiver, not the source) closer to the source than the
+ *          receiver and within h_k of the segment (distance b) adds
+ *          kappa_k 3 m_k (1 - b / h_k) / (pi h_k^2).  A sphere holding more
+ *          than 4096 particles gives EUNSUPPORTED.  trevr2_J_backward, the
+ *          batches and trevr2_J_noalloc take neither flag (EUNSUPPORTED,
+ *          EUNSUPPORTED, EINVAL).
  *  J       [A][nbsel] float32 output, overwritten
  * Active indices outside [0, N) give EINVAL (their rows are set to NaN).
  * Without TREVR2_ASYNC the call synchronises `stream` and returns any device

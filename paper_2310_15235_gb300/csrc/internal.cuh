@@ -52,6 +52,7 @@ constexpr uint32_t kStatusStackOverflow = 1u << 1;
 constexpr uint32_t kStatusBadInput = 1u << 2;
 constexpr uint32_t kStatusOutsideBox = 1u << 3;
 constexpr uint32_t kStatusTimeout = 1u << 4;
+constexpr uint32_t kStatusPPOverflow = 1u << 5;  // a p-p sphere held too many particles
 
 // Geometry of the transmission average for one cell shape and one beam pair:
 // weights V1/V (= V2/V), V12/V and the chord through the centre of a cell of

@@ -46,7 +46,8 @@ namespace trevr2 {
 template <int NBP, bool kBucket = false>
 __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int* lstk,
                              const SrcEntry* V, float* T, const int* off, const int* order,
-                             int nbeams, int* next_beam, const NodeW* chain, int leaf) {
+                             int nbeams, int* next_beam, const NodeW* chain, int leaf,
+                             float rpp = 0.0f) {
   int idx = lane;
   for (;;) {
     if (idx >= nbeams) break;
@@ -67,6 +68,9 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
     for (int b = 0; b < NBP; ++b) tau[b] = 0.0f;
     // a cell of the cut crossed on [t0, t1): sources inside it, then its tau
     auto segment = [&](int q, const NodeW& nd, float t0, float t1) {
+      // with a p-p radius (Sec. 2.4), cells absorb only beyond it
+      if constexpr (kBucket) t0 = fmaxf(t0, rpp);
+      if constexpr (kBucket) t1 = fmaxf(t1, t0);
       const BandVec<NBP> al = (nd.meta & kMetaLeaf)
                                   ? load_bands<NBP>(a.alpha_leaf + int64_t(q) * NBP)
                                   : load_bands<NBP>(a.alpha_tab + (int64_t(nd.aux) * a.P + pair) * NBP);
@@ -110,7 +114,7 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
       const NodeW nd = a.nodes[q];
       float t0, t1;
       if (!beam_chord(nd, xv, n, inv, smax, t0, t1)) continue;
-      if (!(nd.meta & kMetaLeaf) && cell_opens<kBucket>(a, q, nd, x, si)) {
+      if (!(nd.meta & kMetaLeaf) && cell_opens<kBucket>(a, q, nd, x, si, rpp)) {
         // the crossed halves, the near one (the side of the receiver) on top
         bool lower_first, lower_hit, upper_hit;
         float lt0, lt1, ut0, ut1;
@@ -267,6 +271,14 @@ struct BucketArgs {
   const uint64_t* keys;  // [A] sorted element position of each slot (N: invalid)
   const int* leaf;       // [A] leaf of each slot (-1: invalid)
   uint32_t rflags;       // the receivers' flags (TREVR2_SOFT, TREVR2_THICK)
+  // particle-particle absorption (TREVR2_PP, Sec. 2.4)
+  int pp;                // 0: off
+  int pp_cap;            // p-p particles a warp holds
+  double beam;           // sqrt(4 pi / N_ray): beam width per unit distance
+  const float* mass;     // [N] sorted
+  float4* pp_xh;         // [warps][pp_cap] position, h
+  float4* pp_kc;         // [warps][pp_cap] kappa_b m 3 / (pi h^2) per band
+  int* pp_si;            // [warps][pp_cap] sorted element index
 };
 
 // The leaf holding each slot's element: down the tree by the first element
@@ -286,18 +298,186 @@ __global__ void k_bucket_leaf(const int* __restrict__ child, const int* __restri
   leaf[p] = q;
 }
 
-// The staged sources against the bucket's receivers (one per lane j < nrec,
-// position xr, size hr): per receiver, all lanes over the sources with a
-// compensated FP32 sum, reduced in FP64 into acc of lane j.
+// The bucket's p-p radius and particles (Sec. 2.4): from the radius of the
+// sphere through the leaf's corners, the radius grows to h_j / beam for the
+// largest gas element j inside until nothing inside is wider than the beam
+// there.  Membership is decided in FP64 on the FP64 positions.  The warp
+// walks the cells that reach the sphere; lane 0 of the warp's origin slot
+// gets the FP64 radius, and the particles go to the warp's p-p arrays.
+// Returns their count (warp-uniform).
 template <int NBP>
+__device__ int collect_pp(const WalkArgs& a, const BucketArgs& bk, const double* o64, double r0,
+                          int lane, int* stk, int64_t gw, double& rpp) {
+  float4* xh = bk.pp_xh + gw * bk.pp_cap;
+  float4* kc = bk.pp_kc + gw * bk.pp_cap;
+  int* psi = bk.pp_si + gw * bk.pp_cap;
+  const float3 o = make_float3(float(o64[0]), float(o64[1]), float(o64[2]));
+  const unsigned lt = (1u << lane) - 1u;
+  double r = r0;
+  int n = 0;
+  for (int it = 0; it < 64; ++it) {
+    // the gas elements within r of the centre, and the largest h among them
+    const float rf = float(r) * (1.0f + 1e-5f) + 1e-7f;  // box test: never too tight
+    n = 0;
+    float H = 0.0f;
+    int sp = 1;
+    if (lane == 0) stk[0] = 0;
+    __syncwarp();
+    while (sp > 0) {
+      const int k = min(32, sp);
+      const int q = lane < k ? stk[sp - 1 - lane] : -1;
+      sp -= k;
+      __syncwarp();
+      int npush = 0, child = -1, first = 0, count = 0;
+      if (q >= 0) {
+        const NodeW nd = a.nodes[q];
+        const float3 e = node_ext(nd.meta);
+        const float dx = fmaxf(0.0f, fmaxf(nd.lo[0] - o.x, o.x - (nd.lo[0] + e.x)));
+        const float dy = fmaxf(0.0f, fmaxf(nd.lo[1] - o.y, o.y - (nd.lo[1] + e.y)));
+        const float dz = fmaxf(0.0f, fmaxf(nd.lo[2] - o.z, o.z - (nd.lo[2] + e.z)));
+        if (dx * dx + dy * dy + dz * dz < rf * rf && nd.count > 0) {
+          if (nd.meta & kMetaLeaf) {
+            first = nd.aux;
+            count = nd.count;
+          } else {
+            npush = 2;
+            child = nd.child;
+          }
+        }
+      }
+      const int incl = warp_incl_scan(npush, lane);
+      const int tot = __shfl_sync(0xffffffffu, incl, 31);
+      if (npush) {
+        const int pos = sp + incl - npush;
+        if (pos + 2 <= a.stack_ints) {
+          stk[pos] = child + 1;
+          stk[pos + 1] = child;
+        } else {
+          atomicOr(a.status, kStatusStackOverflow);
+        }
+      }
+      sp = min(sp + tot, a.stack_ints);
+      int maxc = count;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) maxc = max(maxc, __shfl_xor_sync(0xffffffffu, maxc, off));
+      for (int e = 0; e < maxc; ++e) {
+        bool in = false;
+        const int sj = first + e;
+        if (e < count && bk.mass[sj] > 0.0f) {
+          const double* p = a.pos64 + 3 * int64_t(sj);
+          double d2 = 0.0;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const double dd = __dsub_rn(p[c], o64[c]);
+            d2 = __dadd_rn(d2, __dmul_rn(dd, dd));
+          }
+          in = sqrt(d2) < r;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (in) {
+          const int idx = n + __popc(m & lt);
+          const float h = a.hn[sj];
+          H = fmaxf(H, h);
+          if (idx < bk.pp_cap) {
+            const float4 pj = a.pos32[sj];
+            xh[idx] = make_float4(pj.x, pj.y, pj.z, h);
+            // kappa m is in caller units, h normalised: 3/(pi h^2) in caller units
+            const float c = float(3.0 / (3.14159265358979 * double(h) * double(h)) * a.inv_size2);
+            float kv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int b = 0; b < NBP; ++b) kv[b] = a.km[int64_t(sj) * NBP + b] * c;
+            kc[idx] = make_float4(kv[0], kv[1], kv[2], kv[3]);
+            psi[idx] = sj;
+          }
+        }
+        n += __popc(m);
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) H = fmaxf(H, __shfl_xor_sync(0xffffffffu, H, off));
+    const double grown = fmax(r, double(H) / bk.beam);
+    if (grown == r) break;
+    r = grown;
+  }
+  if (n > bk.pp_cap) {
+    if (lane == 0) atomicOr(a.status, kStatusPPOverflow);
+    n = bk.pp_cap;
+  }
+  rpp = r;
+  __syncwarp();
+  return n;
+}
+
+// The p-p optical depth, per band, of the segment from a receiver at x
+// (sorted index si) to a source at p (its element sj, or -1), r = |p - x|:
+// every p-p particle k other than those two that is closer to the source
+// than the receiver and within h_k of the segment (distance b) adds
+// kappa_k 3 m_k / (pi h_k^2) (1 - b / h_k).  The column goes to zero at
+// b = h_k, so that test needs no care; "closer" is decided in FP32 and again
+// in FP64 (positions pos64 of the receiver, p64 of the source) inside a
+// guard band that covers the FP32 error.
+template <int NBP>
+__device__ __forceinline__ void pp_tau(const WalkArgs& a, int npp, const float4* xh,
+                                       const float4* kc, const int* psi, float3 x, int si,
+                                       float4 p, const double* p64, int sj, float r,
+                                       float* tau) {
+  const float vx = p.x - x.x, vy = p.y - x.y, vz = p.z - x.z;
+  const float r2 = r * r;
+  const float ir2 = 1.0f / r2;
+  const float guard = 2e-6f * r + 1e-7f;
+  for (int k = 0; k < npp; ++k) {
+    const float4 q = xh[k];
+    const float wx = q.x - x.x, wy = q.y - x.y, wz = q.z - x.z;
+    float t = (wx * vx + wy * vy + wz * vz) * ir2;
+    t = fminf(fmaxf(t, 0.0f), 1.0f);
+    const float ex = wx - t * vx, ey = wy - t * vy, ez = wz - t * vz;
+    const float b2 = ex * ex + ey * ey + ez * ez;
+    if (!(b2 < q.w * q.w)) continue;
+    const int kk = psi[k];
+    if (kk == si || kk == sj) continue;
+    const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+    const float dj2 = dx * dx + dy * dy + dz * dz;
+    bool front;
+    if (fabsf(r2 - dj2) > guard * (r + sqrtf(dj2))) {
+      front = dj2 < r2;
+    } else {  // FP64: |x_k - p| < |x - p|
+      const double* xk = a.pos64 + 3 * int64_t(kk);
+      const double* xi = a.pos64 + 3 * int64_t(si);
+      double d2k = 0.0, d2i = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        const double dk = __dsub_rn(xk[c], p64[c]);
+        const double di = __dsub_rn(xi[c], p64[c]);
+        d2k = __dadd_rn(d2k, __dmul_rn(dk, dk));
+        d2i = __dadd_rn(d2i, __dmul_rn(di, di));
+      }
+      front = sqrt(d2k) < sqrt(d2i);
+    }
+    if (!front) continue;
+    const float f = 1.0f - sqrtf(b2) / q.w;
+    const float4 c = kc[k];
+    const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int bb = 0; bb < NBP; ++bb) tau[bb] += cv[bb] * f;
+  }
+}
+
+// The staged sources against the bucket's receivers (one per lane j < nrec,
+// position xr, size hr, sorted index sir): per receiver, all lanes over the
+// sources with a compensated FP32 sum, reduced in FP64 into acc of lane j.
+// With kPP the npp p-p particles add their optical depth (pp_tau).
+template <int NBP, bool kPP>
 __device__ __forceinline__ void eval_bucket(const WalkArgs& a, bool soft, int lane,
                                             const SrcEntry* V, const float* T, int n, int nrec,
-                                            float4 xr, float hr, double* acc) {
+                                            float4 xr, float hr, int sir, double* acc,
+                                            int npp, const float4* ppxh, const float4* ppkc,
+                                            const int* ppsi) {
   for (int j = 0; j < nrec; ++j) {
     const float xx = __shfl_sync(0xffffffffu, xr.x, j);
     const float xy = __shfl_sync(0xffffffffu, xr.y, j);
     const float xz = __shfl_sync(0xffffffffu, xr.z, j);
     const float hh = __shfl_sync(0xffffffffu, hr, j);
+    const int si = __shfl_sync(0xffffffffu, sir, j);
     float Js[NBP], Jc[NBP];
 #pragma unroll
     for (int b = 0; b < NBP; ++b) Js[b] = Jc[b] = 0.0f;
@@ -314,9 +494,15 @@ __device__ __forceinline__ void eval_bucket(const WalkArgs& a, bool soft, int la
       const float rs = r / src.s;
       const BandVec<NBP> L = load_bands<NBP>(elem ? a.Lelem + id * NBP : a.Lnode + id * NBP);
       const BandVec<NBP> tk = load_bands<NBP>(T + int64_t(e) * NBP);
+      float tpp[NBP];
+#pragma unroll
+      for (int b = 0; b < NBP; ++b) tpp[b] = 0.0f;
+      if constexpr (kPP)
+        pp_tau<NBP>(a, npp, ppxh, ppkc, ppsi, make_float3(xx, xy, xz), si, p,
+                    elem ? a.pos64 + 3 * id : a.c64 + 3 * id, elem ? int(id) : -1, r, tpp);
 #pragma unroll
       for (int b = 0; b < NBP; ++b) {
-        const float term = L.v[b] * w * expf(-tk.v[b] * rs);
+        const float term = L.v[b] * w * expf(-(tk.v[b] * rs + tpp[b]));
         const float y = term - Jc[b];
         const float t = Js[b] + y;
         Jc[b] = (t - Js[b]) - y;
@@ -333,8 +519,9 @@ __device__ __forceinline__ void eval_bucket(const WalkArgs& a, bool soft, int la
   }
 }
 
-// J of the receivers in slots [p0, p1), all in leaf q, into their rows.
-template <int NBP>
+// J of the receivers in slots [p0, p1), all in leaf q, into their rows
+// (kPP: with the p-p absorption of Sec. 2.4).
+template <int NBP, bool kPP>
 __device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0, int64_t p1,
                             int q, int64_t gw, int lane, int* stk, int* off, int* next_beam,
                             int* lstk, SrcEntry* U, int* Up, SrcEntry* V, float* T) {
@@ -358,9 +545,24 @@ __device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0,
   NodeW* chain = reinterpret_cast<NodeW*>(off + 2 * a.npix + 36);
   const int leaf = build_chain(a.nodes, o, lane, chain);  // == q
   const bool soft = (bk.rflags & TREVR2_SOFT) != 0;
+  // Sec. 2.4: the bucket's p-p radius and particles
+  int npp = 0;
+  float rpp = 0.0f;
+  if constexpr (kPP) {
+    const double r0 = 0.5 * sqrt(double(e.x) * e.x + double(e.y) * e.y + double(e.z) * e.z);
+    double r64 = 0.0;
+    __syncwarp();
+    npp = collect_pp<NBP>(a, bk, a.origin64 + 4 * gw, r0, lane, stk, gw, r64);
+    if (lane == 0) a.origin64[4 * gw + 3] = r64;
+    rpp = float(r64);
+    __syncwarp();
+  }
+  const float4* ppxh = bk.pp_xh + gw * bk.pp_cap;
+  const float4* ppkc = bk.pp_kc + gw * bk.pp_cap;
+  const int* ppsi = bk.pp_si + gw * bk.pp_cap;
   for (int64_t c0 = p0; c0 < p1; c0 += 32) {
     const int nrec = int(min(int64_t(32), p1 - c0));
-    int si = 0;
+    int si = -1;
     float4 xr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float hr = 1.0f;
     if (lane < nrec) {
@@ -372,7 +574,7 @@ __device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0,
 #pragma unroll
     for (int b = 0; b < NBP; ++b) acc[b] = 0.0;
     for (int lo = 0;; lo += a.M) {
-      const int total = phase_sources<true>(a, o, si_o, lane, stk, a.stack_ints, U, Up, lo);
+      const int total = phase_sources<true>(a, o, si_o, lane, stk, a.stack_ints, U, Up, lo, rpp);
       const int staged = min(total - lo, a.M);
       make_sources<true>(a, o, si_o, lane, U, Up, staged);
       const int n = staged > 0 ? bin_sources(a, lane, U, Up, staged, V, off) : 0;
@@ -382,9 +584,10 @@ __device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0,
         if (lane == 0) *next_beam = 32;
         __syncwarp();
         phase_absorb<NBP, true>(a, o, si_o, lane, lstk, V, T, off, order, nbeams, next_beam,
-                                chain, leaf);
+                                chain, leaf, rpp);
         __syncwarp();
-        eval_bucket<NBP>(a, soft, lane, V, T, n, nrec, xr, hr, acc);
+        eval_bucket<NBP, kPP>(a, soft, lane, V, T, n, nrec, xr, hr, si, acc, npp, ppxh, ppkc,
+                              ppsi);
         __syncwarp();
       }
       if (lo + a.M >= total) break;
@@ -410,7 +613,7 @@ __device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0,
 }
 
 // One warp per bucket; slots from a global counter.
-template <int NBP, int WARPS>
+template <int NBP, int WARPS, bool kPP>
 __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS)
     k_walk_bucket(WalkArgs a, const __grid_constant__ BucketArgs bk) {
   extern __shared__ int smem[];
@@ -445,7 +648,7 @@ __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS)
       p1 += __ffs(~same) - 1;
       break;
     }
-    walk_bucket<NBP>(a, bk, p0, p1, q, gw, lane, stk, off, next_beam, lstk, U, Up, V, T);
+    walk_bucket<NBP, kPP>(a, bk, p0, p1, q, gw, lane, stk, off, next_beam, lstk, U, Up, V, T);
   }
 }
 
@@ -723,9 +926,14 @@ static int launch_walk(Tree* t, Table* tb, const int64_t* active, int64_t A, int
 }
 
 template <int NBP>
-static const void* bucket_kernel_nbp() {
-  return reinterpret_cast<const void*>(&k_walk_bucket<NBP, kWalkWarps>);
+static const void* bucket_kernel_nbp(bool pp) {
+  return pp ? reinterpret_cast<const void*>(&k_walk_bucket<NBP, kWalkWarps, true>)
+            : reinterpret_cast<const void*>(&k_walk_bucket<NBP, kWalkWarps, false>);
 }
+
+// p-p particles one warp holds for a bucket (TREVR2_PP); a bucket whose
+// sphere holds more is reported (EUNSUPPORTED).
+constexpr int kPPCapacity = 4096;
 
 // TREVR2_BUCKET: receivers in Morton order, the leaf of each, one warp per
 // bucket.
@@ -763,11 +971,16 @@ static int launch_walk_bucket(Tree* t, Table* tb, const int64_t* active, int64_t
   note_launch();
   a.order = slots;
   BucketArgs bk;
+  std::memset(&bk, 0, sizeof(bk));
   bk.keys = keys;
   bk.leaf = leaf;
   bk.rflags = flags & (TREVR2_SOFT | TREVR2_THICK);
-  const void* fn = t->nbp == 1 ? bucket_kernel_nbp<1>()
-                 : t->nbp == 2 ? bucket_kernel_nbp<2>() : bucket_kernel_nbp<4>();
+  bk.pp = (flags & TREVR2_PP) != 0;
+  bk.pp_cap = bk.pp ? kPPCapacity : 0;
+  bk.beam = std::sqrt(4.0 * M_PI / double(a.npix));
+  bk.mass = t->mass;
+  const void* fn = t->nbp == 1 ? bucket_kernel_nbp<1>(bk.pp)
+                 : t->nbp == 2 ? bucket_kernel_nbp<2>(bk.pp) : bucket_kernel_nbp<4>(bk.pp);
   const size_t smem = walk_smem(kWalkWarps, a.stack_ints, a.npix, a.max_depth);
   int per_sm = 0, sms = 0;
   T2_CHECK(config_walk_kernel(fn, kWalkWarps, smem, &per_sm, &sms));
@@ -776,7 +989,9 @@ static int launch_walk_bucket(Tree* t, Table* tb, const int64_t* active, int64_t
   blocks = std::max<int64_t>(blocks, 1);
   const size_t warps = size_t(blocks) * kWalkWarps;
   const size_t wb = (walk_buffer_bytes(warps, a.M) + 255) & ~size_t(255);
-  const size_t need = wb + warps * 4 * sizeof(double);
+  const size_t ob = (warps * 4 * sizeof(double) + 255) & ~size_t(255);
+  const size_t pb = warps * size_t(bk.pp_cap) * (2 * sizeof(float4) + sizeof(int));
+  const size_t need = wb + ob + pb;
   if (t->scratch_bytes < need) {
     if (t->scratch) cudaFreeAsync(t->scratch, st);
     t->scratch = nullptr;
@@ -787,6 +1002,12 @@ static int launch_walk_bucket(Tree* t, Table* tb, const int64_t* active, int64_t
   }
   place_walk_buffers(static_cast<char*>(t->scratch), warps, a.M, &a.srcU, &a.srcV, &a.srcT, &a.pixU);
   a.origin64 = reinterpret_cast<double*>(static_cast<char*>(t->scratch) + wb);
+  if (bk.pp) {
+    char* pp = static_cast<char*>(t->scratch) + wb + ob;
+    bk.pp_xh = reinterpret_cast<float4*>(pp);
+    bk.pp_kc = bk.pp_xh + warps * bk.pp_cap;
+    bk.pp_si = reinterpret_cast<int*>(bk.pp_kc + warps * bk.pp_cap);
+  }
   T2_CUDA(cudaMemsetAsync(t->counter, 0, sizeof(unsigned long long), st));
   void* args[] = {&a, &bk};
   T2_CUDA(cudaLaunchKernel(fn, dim3(unsigned(blocks)), dim3(kWalkWarps * 32), args, smem, st));
@@ -807,6 +1028,11 @@ int read_status(Tree* t, cudaStream_t st) {
   if (s & kStatusStackOverflow) {
     set_error("trevr2_J: internal traversal stack overflow");
     return TREVR2_EINTERNAL;
+  }
+  if (s & kStatusPPOverflow) {
+    set_error("trevr2_J: a bucket's p-p sphere holds more than %d particles (TREVR2_PP)",
+              kPPCapacity);
+    return TREVR2_EUNSUPPORTED;
   }
   set_error("trevr2: device status 0x%x", s);
   return TREVR2_EINTERNAL;
@@ -838,8 +1064,13 @@ extern "C" int trevr2_J(trevr2_tree* tree, const int64_t* active, int64_t A, int
     set_error("trevr2_J: theta must be positive and finite");
     return TREVR2_EINVAL;
   }
-  if (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_ASYNC | TREVR2_BUCKET)) {
+  if (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_ASYNC | TREVR2_BUCKET |
+                TREVR2_PP)) {
     set_error("trevr2_J: unknown flag bits 0x%x", flags);
+    return TREVR2_EINVAL;
+  }
+  if ((flags & TREVR2_PP) && !(flags & TREVR2_BUCKET)) {
+    set_error("trevr2_J: TREVR2_PP needs TREVR2_BUCKET");
     return TREVR2_EINVAL;
   }
   int bsel[TREVR2_MAX_BANDS];
@@ -991,8 +1222,8 @@ extern "C" int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const 
               TREVR2_MAX_NSIDE);
     return nside > TREVR2_MAX_NSIDE ? TREVR2_EUNSUPPORTED : TREVR2_EINVAL;
   }
-  if (flags & TREVR2_BUCKET) {
-    set_error("trevr2_batch_create: TREVR2_BUCKET is a trevr2_J flag only");
+  if (flags & (TREVR2_BUCKET | TREVR2_PP)) {
+    set_error("trevr2_batch_create: TREVR2_BUCKET and TREVR2_PP are trevr2_J flags only");
     return TREVR2_EUNSUPPORTED;
   }
   if (!(theta > 0.0f) || !std::isfinite(theta) || (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_ASYNC))) {

@@ -201,17 +201,48 @@ __device__ __forceinline__ const double* origin64(const WalkArgs& a, int si) {
   return a.pos64 + 3 * int64_t(si);
 }
 
+// FP64 distance from the FP64 origin x64 to a box, the definition without
+// contraction, below r?
+static __device__ __noinline__ bool box_within64(const double* __restrict__ x64, double r,
+                                                 float lx, float ly, float lz, uint32_t meta) {
+  const float3 e = node_ext(meta);
+  const double ext[3] = {double(e.x), double(e.y), double(e.z)};
+  const double lo3[3] = {double(lx), double(ly), double(lz)};
+  double s = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const double lo = lo3[k], hi = __dadd_rn(lo, ext[k]);
+    double dd = 0.0;
+    if (x64[k] < lo) dd = __dsub_rn(lo, x64[k]);
+    else if (x64[k] > hi) dd = __dsub_rn(x64[k], hi);
+    s = __dadd_rn(s, __dmul_rn(dd, dd));
+  }
+  return sqrt(s) < r;
+}
+
 // Sec. 2.5.2: open iff d == 0 or B > theta d, seen from x (receiver si, or
-// with kBucket the centre of the bucket that warp -1 - si walks).
+// with kBucket the centre of the bucket that warp -1 - si walks).  With
+// kBucket and rpp > 0 (Sec. 2.4) a cell within the bucket's p-p radius opens
+// too; the FP64 radius is the fourth word of the warp's origin slot.
 template <bool kBucket = false>
 __device__ __forceinline__ bool cell_opens(const WalkArgs& a, int q, const NodeW& nd, float3 x,
-                                           int si) {
+                                           int si, float rpp = 0.0f) {
   const float3 e = node_ext(nd.meta);
   const float dx = fmaxf(0.0f, fmaxf(nd.lo[0] - x.x, x.x - (nd.lo[0] + e.x)));
   const float dy = fmaxf(0.0f, fmaxf(nd.lo[1] - x.y, x.y - (nd.lo[1] + e.y)));
   const float dz = fmaxf(0.0f, fmaxf(nd.lo[2] - x.z, x.z - (nd.lo[2] + e.z)));
   const float d2 = dx * dx + dy * dy + dz * dz;
   if (d2 == 0.0f) return true;
+  if constexpr (kBucket) {
+    if (rpp > 0.0f) {
+      const float m = d2 - rpp * rpp;
+      if (fabsf(m) <= 1e-5f * rpp * rpp) {
+        const double* o = origin64<true>(a, si);
+        if (box_within64(o, o[3], nd.lo[0], nd.lo[1], nd.lo[2], nd.meta)) return true;
+      } else if (m < 0.0f) {
+        return true;
+      }
+    }
+  }
   const float B = nd.B;
   const float margin = B * B - a.theta2 * d2;
   const float g = 2.2f * B * (a.guard_abs + a.guard_rel * B);
@@ -287,7 +318,7 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 // sources of this receiver (warp-uniform).
 template <bool kBucket = false>
 static __device__ int phase_sources(const WalkArgs& a, float3 x, int si, int lane, int* stk, int cap,
-                             SrcEntry* U, int* Up, int lo) {
+                             SrcEntry* U, int* Up, int lo, float rpp = 0.0f) {
   int sp = 1;
   if (lane == 0) stk[0] = 0;
   __syncwarp();
@@ -303,7 +334,7 @@ static __device__ int phase_sources(const WalkArgs& a, float3 x, int si, int lan
     if (q >= 0) {
       const NodeW nd = a.nodes[q];
       if (nd.meta & kMetaHasL) {
-        if (!cell_opens<kBucket>(a, q, nd, x, si)) {
+        if (!cell_opens<kBucket>(a, q, nd, x, si, rpp)) {
           emit_node = true;
         } else if (nd.meta & kMetaLeaf) {
           leaf_first = nd.aux;
