@@ -43,7 +43,7 @@ namespace trevr2 {
 // crossed far halves go on the stack.  The stack walk then takes the far
 // halves, nearest first.  This visits the same cells in the same order as a
 // walk from the root.
-template <int NBP, bool kBucket = false>
+template <int NBP, bool kBucket = false, bool kPP = false>
 __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int* lstk,
                              const SrcEntry* V, float* T, const int* off, const int* order,
                              int nbeams, int* next_beam, const NodeW* chain, int leaf,
@@ -69,8 +69,8 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
     // a cell of the cut crossed on [t0, t1): sources inside it, then its tau
     auto segment = [&](int q, const NodeW& nd, float t0, float t1) {
       // with a p-p radius (Sec. 2.4), cells absorb only beyond it
-      if constexpr (kBucket) t0 = fmaxf(t0, rpp);
-      if constexpr (kBucket) t1 = fmaxf(t1, t0);
+      if constexpr (kPP) t0 = fmaxf(t0, rpp);
+      if constexpr (kPP) t1 = fmaxf(t1, t0);
       const BandVec<NBP> al = (nd.meta & kMetaLeaf)
                                   ? load_bands<NBP>(a.alpha_leaf + int64_t(q) * NBP)
                                   : load_bands<NBP>(a.alpha_tab + (int64_t(nd.aux) * a.P + pair) * NBP);
@@ -114,7 +114,7 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
       const NodeW nd = a.nodes[q];
       float t0, t1;
       if (!beam_chord(nd, xv, n, inv, smax, t0, t1)) continue;
-      if (!(nd.meta & kMetaLeaf) && cell_opens<kBucket>(a, q, nd, x, si, rpp)) {
+      if (!(nd.meta & kMetaLeaf) && cell_opens<kBucket, kPP>(a, q, nd, x, si, rpp)) {
         // the crossed halves, the near one (the side of the receiver) on top
         bool lower_first, lower_hit, upper_hit;
         float lt0, lt1, ut0, ut1;
@@ -279,6 +279,7 @@ struct BucketArgs {
   float4* pp_xh;         // [warps][pp_cap] position, h
   float4* pp_kc;         // [warps][pp_cap] kappa_b m 3 / (pi h^2) per band
   int* pp_si;            // [warps][pp_cap] sorted element index
+  float4* pp_w;          // [warps][pp_cap] per receiver: x_k - x, |x_k - x|^2 - h_k^2
 };
 
 // The leaf holding each slot's element: down the tree by the first element
@@ -410,32 +411,34 @@ __device__ int collect_pp(const WalkArgs& a, const BucketArgs& bk, const double*
 }
 
 // The p-p optical depth, per band, of the segment from a receiver at x
-// (sorted index si) to a source at p (its element sj, or -1), r = |p - x|:
-// every p-p particle k other than those two that is closer to the source
-// than the receiver and within h_k of the segment (distance b) adds
-// kappa_k 3 m_k / (pi h_k^2) (1 - b / h_k).  The column goes to zero at
+// (sorted index si) to a source at p (its element sj, or -1), v = p - x,
+// r = |v|: every p-p particle k other than those two that is closer to the
+// source than the receiver and within h_k of the segment (distance b) adds
+// kappa_k 3 m_k / (pi h_k^2) (1 - b / h_k).  pw[k] = (w, |w|^2 - h_k^2) with
+// w = x_k - x, set per receiver: with t the clamped segment parameter of
+// the closest point, |w|^2 - b^2 = t (2 w.v - t r^2), so most particles are
+// rejected with one load and a few products.  The column goes to zero at
 // b = h_k, so that test needs no care; "closer" is decided in FP32 and again
 // in FP64 (positions pos64 of the receiver, p64 of the source) inside a
 // guard band that covers the FP32 error.
 template <int NBP>
-__device__ __forceinline__ void pp_tau(const WalkArgs& a, int npp, const float4* xh,
-                                       const float4* kc, const int* psi, float3 x, int si,
-                                       float4 p, const double* p64, int sj, float r,
-                                       float* tau) {
-  const float vx = p.x - x.x, vy = p.y - x.y, vz = p.z - x.z;
+__device__ __forceinline__ void pp_tau(const WalkArgs& a, int npp, const float4* pw,
+                                       const float4* xh, const float4* kc, const int* psi,
+                                       int si, float4 p, const double* p64, int sj, float vx,
+                                       float vy, float vz, float r, float* tau) {
   const float r2 = r * r;
   const float ir2 = 1.0f / r2;
   const float guard = 2e-6f * r + 1e-7f;
+#pragma unroll 4
   for (int k = 0; k < npp; ++k) {
-    const float4 q = xh[k];
-    const float wx = q.x - x.x, wy = q.y - x.y, wz = q.z - x.z;
-    float t = (wx * vx + wy * vy + wz * vz) * ir2;
-    t = fminf(fmaxf(t, 0.0f), 1.0f);
-    const float ex = wx - t * vx, ey = wy - t * vy, ez = wz - t * vz;
-    const float b2 = ex * ex + ey * ey + ez * ez;
-    if (!(b2 < q.w * q.w)) continue;
+    const float4 w = pw[k];
+    const float dot = w.x * vx + w.y * vy + w.z * vz;
+    const float t = fminf(fmaxf(dot * ir2, 0.0f), 1.0f);
+    const float g = t * (2.0f * dot - t * r2);  // |w|^2 - b^2
+    if (!(g > w.w)) continue;                   // b >= h_k
     const int kk = psi[k];
     if (kk == si || kk == sj) continue;
+    const float4 q = xh[k];
     const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
     const float dj2 = dx * dx + dy * dy + dz * dz;
     bool front;
@@ -454,7 +457,8 @@ __device__ __forceinline__ void pp_tau(const WalkArgs& a, int npp, const float4*
       front = sqrt(d2k) < sqrt(d2i);
     }
     if (!front) continue;
-    const float f = 1.0f - sqrtf(b2) / q.w;
+    const float b2 = fmaxf(0.0f, (w.w + q.w * q.w) - g);
+    const float f = fmaxf(0.0f, 1.0f - sqrtf(b2) / q.w);
     const float4 c = kc[k];
     const float cv[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
@@ -471,13 +475,21 @@ __device__ __forceinline__ void eval_bucket(const WalkArgs& a, bool soft, int la
                                             const SrcEntry* V, const float* T, int n, int nrec,
                                             float4 xr, float hr, int sir, double* acc,
                                             int npp, const float4* ppxh, const float4* ppkc,
-                                            const int* ppsi) {
+                                            const int* ppsi, float4* ppw) {
   for (int j = 0; j < nrec; ++j) {
     const float xx = __shfl_sync(0xffffffffu, xr.x, j);
     const float xy = __shfl_sync(0xffffffffu, xr.y, j);
     const float xz = __shfl_sync(0xffffffffu, xr.z, j);
     const float hh = __shfl_sync(0xffffffffu, hr, j);
     const int si = __shfl_sync(0xffffffffu, sir, j);
+    if constexpr (kPP) {  // the p-p particles seen from this receiver
+      for (int k = lane; k < npp; k += 32) {
+        const float4 q = ppxh[k];
+        const float wx = q.x - xx, wy = q.y - xy, wz = q.z - xz;
+        ppw[k] = make_float4(wx, wy, wz, (wx * wx + wy * wy + wz * wz) - q.w * q.w);
+      }
+      __syncwarp();
+    }
     float Js[NBP], Jc[NBP];
 #pragma unroll
     for (int b = 0; b < NBP; ++b) Js[b] = Jc[b] = 0.0f;
@@ -491,15 +503,16 @@ __device__ __forceinline__ void eval_bucket(const WalkArgs& a, bool soft, int la
       if (!(r2 > 0.0f)) continue;  // the receiver itself, or on top of it
       const float r = sqrtf(r2);
       const float w = soft ? soft_kernel(r, hh) : 1.0f / (kFourPi * r2);
-      const float rs = r / src.s;
-      const BandVec<NBP> L = load_bands<NBP>(elem ? a.Lelem + id * NBP : a.Lnode + id * NBP);
-      const BandVec<NBP> tk = load_bands<NBP>(T + int64_t(e) * NBP);
       float tpp[NBP];
 #pragma unroll
       for (int b = 0; b < NBP; ++b) tpp[b] = 0.0f;
       if constexpr (kPP)
-        pp_tau<NBP>(a, npp, ppxh, ppkc, ppsi, make_float3(xx, xy, xz), si, p,
-                    elem ? a.pos64 + 3 * id : a.c64 + 3 * id, elem ? int(id) : -1, r, tpp);
+        pp_tau<NBP>(a, npp, ppw, ppxh, ppkc, ppsi, si, p,
+                    elem ? a.pos64 + 3 * id : a.c64 + 3 * id, elem ? int(id) : -1, vx, vy, vz,
+                    r, tpp);
+      const float rs = r / src.s;
+      const BandVec<NBP> L = load_bands<NBP>(elem ? a.Lelem + id * NBP : a.Lnode + id * NBP);
+      const BandVec<NBP> tk = load_bands<NBP>(T + int64_t(e) * NBP);
 #pragma unroll
       for (int b = 0; b < NBP; ++b) {
         const float term = L.v[b] * w * expf(-(tk.v[b] * rs + tpp[b]));
@@ -516,6 +529,7 @@ __device__ __forceinline__ void eval_bucket(const WalkArgs& a, bool soft, int la
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if (lane == j) acc[b] += v;
     }
+    if constexpr (kPP) __syncwarp();  // ppw is rewritten for the next receiver
   }
 }
 
@@ -560,6 +574,7 @@ __device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0,
   const float4* ppxh = bk.pp_xh + gw * bk.pp_cap;
   const float4* ppkc = bk.pp_kc + gw * bk.pp_cap;
   const int* ppsi = bk.pp_si + gw * bk.pp_cap;
+  float4* ppw = bk.pp_w + gw * bk.pp_cap;
   for (int64_t c0 = p0; c0 < p1; c0 += 32) {
     const int nrec = int(min(int64_t(32), p1 - c0));
     int si = -1;
@@ -574,7 +589,8 @@ __device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0,
 #pragma unroll
     for (int b = 0; b < NBP; ++b) acc[b] = 0.0;
     for (int lo = 0;; lo += a.M) {
-      const int total = phase_sources<true>(a, o, si_o, lane, stk, a.stack_ints, U, Up, lo, rpp);
+      const int total = phase_sources<true, kPP>(a, o, si_o, lane, stk, a.stack_ints, U, Up, lo,
+                                                 rpp);
       const int staged = min(total - lo, a.M);
       make_sources<true>(a, o, si_o, lane, U, Up, staged);
       const int n = staged > 0 ? bin_sources(a, lane, U, Up, staged, V, off) : 0;
@@ -583,11 +599,11 @@ __device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0,
         const int nbeams = order_beams(a, lane, V, off, order, order + a.npix);
         if (lane == 0) *next_beam = 32;
         __syncwarp();
-        phase_absorb<NBP, true>(a, o, si_o, lane, lstk, V, T, off, order, nbeams, next_beam,
-                                chain, leaf, rpp);
+        phase_absorb<NBP, true, kPP>(a, o, si_o, lane, lstk, V, T, off, order, nbeams,
+                                     next_beam, chain, leaf, rpp);
         __syncwarp();
         eval_bucket<NBP, kPP>(a, soft, lane, V, T, n, nrec, xr, hr, si, acc, npp, ppxh, ppkc,
-                              ppsi);
+                              ppsi, ppw);
         __syncwarp();
       }
       if (lo + a.M >= total) break;
@@ -990,7 +1006,7 @@ static int launch_walk_bucket(Tree* t, Table* tb, const int64_t* active, int64_t
   const size_t warps = size_t(blocks) * kWalkWarps;
   const size_t wb = (walk_buffer_bytes(warps, a.M) + 255) & ~size_t(255);
   const size_t ob = (warps * 4 * sizeof(double) + 255) & ~size_t(255);
-  const size_t pb = warps * size_t(bk.pp_cap) * (2 * sizeof(float4) + sizeof(int));
+  const size_t pb = warps * size_t(bk.pp_cap) * (3 * sizeof(float4) + sizeof(int));
   const size_t need = wb + ob + pb;
   if (t->scratch_bytes < need) {
     if (t->scratch) cudaFreeAsync(t->scratch, st);
@@ -1006,7 +1022,8 @@ static int launch_walk_bucket(Tree* t, Table* tb, const int64_t* active, int64_t
     char* pp = static_cast<char*>(t->scratch) + wb + ob;
     bk.pp_xh = reinterpret_cast<float4*>(pp);
     bk.pp_kc = bk.pp_xh + warps * bk.pp_cap;
-    bk.pp_si = reinterpret_cast<int*>(bk.pp_kc + warps * bk.pp_cap);
+    bk.pp_w = bk.pp_kc + warps * bk.pp_cap;
+    bk.pp_si = reinterpret_cast<int*>(bk.pp_w + warps * bk.pp_cap);
   }
   T2_CUDA(cudaMemsetAsync(t->counter, 0, sizeof(unsigned long long), st));
   void* args[] = {&a, &bk};

@@ -221,9 +221,9 @@ static __device__ __noinline__ bool box_within64(const double* __restrict__ x64,
 
 // Sec. 2.5.2: open iff d == 0 or B > theta d, seen from x (receiver si, or
 // with kBucket the centre of the bucket that warp -1 - si walks).  With
-// kBucket and rpp > 0 (Sec. 2.4) a cell within the bucket's p-p radius opens
+// kPP and rpp > 0 (Sec. 2.4) a cell within the bucket's p-p radius opens
 // too; the FP64 radius is the fourth word of the warp's origin slot.
-template <bool kBucket = false>
+template <bool kBucket = false, bool kPP = false>
 __device__ __forceinline__ bool cell_opens(const WalkArgs& a, int q, const NodeW& nd, float3 x,
                                            int si, float rpp = 0.0f) {
   const float3 e = node_ext(nd.meta);
@@ -232,7 +232,7 @@ __device__ __forceinline__ bool cell_opens(const WalkArgs& a, int q, const NodeW
   const float dz = fmaxf(0.0f, fmaxf(nd.lo[2] - x.z, x.z - (nd.lo[2] + e.z)));
   const float d2 = dx * dx + dy * dy + dz * dz;
   if (d2 == 0.0f) return true;
-  if constexpr (kBucket) {
+  if constexpr (kBucket && kPP) {
     if (rpp > 0.0f) {
       const float m = d2 - rpp * rpp;
       if (fabsf(m) <= 1e-5f * rpp * rpp) {
@@ -316,7 +316,7 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 // references (a cell index, or an element index with kRefElement) go to
 // U[].ref; make_sources then fills the records.  Returns the total number of
 // sources of this receiver (warp-uniform).
-template <bool kBucket = false>
+template <bool kBucket = false, bool kPP = false>
 static __device__ int phase_sources(const WalkArgs& a, float3 x, int si, int lane, int* stk, int cap,
                              SrcEntry* U, int* Up, int lo, float rpp = 0.0f) {
   int sp = 1;
@@ -334,7 +334,7 @@ static __device__ int phase_sources(const WalkArgs& a, float3 x, int si, int lan
     if (q >= 0) {
       const NodeW nd = a.nodes[q];
       if (nd.meta & kMetaHasL) {
-        if (!cell_opens<kBucket>(a, q, nd, x, si, rpp)) {
+        if (!cell_opens<kBucket, kPP>(a, q, nd, x, si, rpp)) {
           emit_node = true;
         } else if (nd.meta & kMetaLeaf) {
           leaf_first = nd.aux;
