@@ -324,9 +324,25 @@ def run_ours(args, world, rank, local):
             extra["bucket"]["parity_sample"] = {"receivers": 256,
                                                 "median_rel": float(np.median(rel)),
                                                 "max_rel": float(rel.max())}
+            # the paper's full near field: p-p absorption inside r_pp, the
+            # receiver's own column by Eq. taucorr
+            pp_flags = t2.PP | t2.THICK
+            extra["bucket_pp"] = run_bucket(case, inp, dev, walk_avg, reps=2,
+                                            extra_flags=pp_flags, kernel="k_walk_bucket (p-p)")
+            ref = ot.J(sample[:128], case["nside"], case["theta"],
+                       flags=t2.BUCKET | pp_flags, nthreads=cores)
+            got = extra["bucket_pp"].pop("_J")[sample[:128]]
+            rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
+            extra["bucket_pp"]["parity_sample"] = {"receivers": 128,
+                                                   "median_rel": float(np.median(rel)),
+                                                   "max_rel": float(rel.max())}
     elif world == 1 and not args.no_bucket:
         extra["bucket"] = run_bucket(case, inp, dev, walk_avg)
         extra["bucket"].pop("_J")
+        extra["bucket_pp"] = run_bucket(case, inp, dev, walk_avg, reps=2,
+                                        extra_flags=t2.PP | t2.THICK,
+                                        kernel="k_walk_bucket (p-p)")
+        extra["bucket_pp"].pop("_J")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -503,10 +519,11 @@ def run_adjoint(args, dev):
             "backward_units_per_s": units / (bwd * 1e-3)}
 
 
-def run_bucket(case, inp, dev, per_receiver_walk_ms, reps=3):
-    """Per-bucket beams (TREVR2_BUCKET) on the benchmark field: the same J
-    with one walk per leaf from its centre; tree and tables built once, one
-    warm-up and `reps` timed walks."""
+def run_bucket(case, inp, dev, per_receiver_walk_ms, reps=3, extra_flags=0,
+               kernel="k_walk_bucket"):
+    """Per-bucket beams (TREVR2_BUCKET, plus extra_flags) on the benchmark
+    field: the same J with one walk per leaf from its centre; tree and
+    tables built once, one warm-up and `reps` timed walks."""
     import torch
 
     import paper_2310_15235_gb300 as t2
@@ -517,7 +534,7 @@ def run_bucket(case, inp, dev, per_receiver_walk_ms, reps=3):
     A, nb, npix = len(case["active"]), case["nb"], 12 * case["nside"] ** 2
     J = torch.empty((A, nb), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    flags = t2.ASYNC | t2.BUCKET
+    flags = t2.ASYNC | t2.BUCKET | extra_flags
     tree.J(inp["active"], case["nside"], case["theta"], out=J, flags=flags)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -529,7 +546,8 @@ def run_bucket(case, inp, dev, per_receiver_walk_ms, reps=3):
     tree.status()
     ms = e0.elapsed_time(e1) / reps
     out = {"walk_ms": ms, "units_per_s": A * npix * nb / (ms * 1e-3), "unit": UNIT,
-           "kernel": "k_walk_bucket", "speedup_vs_per_receiver": per_receiver_walk_ms / ms,
+           "kernel": kernel, "flags": flags & ~t2.ASYNC,
+           "speedup_vs_per_receiver": per_receiver_walk_ms / ms,
            "_J": J.cpu().numpy()}
     tree.free()
     return out
@@ -593,14 +611,16 @@ def run_walk_only(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         tree.J(inp["active"], case["nside"], case["theta"], out=J,
-               flags=t2.ASYNC | (t2.BUCKET if args.bucket else 0))
+               flags=t2.ASYNC | (t2.BUCKET if args.bucket else 0)
+               | (t2.BUCKET | t2.PP | t2.THICK if args.pp else 0))
         e1.record()
         torch.cuda.synchronize()
         if k >= args.warmup:
             times.append(e0.elapsed_time(e1))
     tree.status()
     ms = float(np.mean(times))
-    print(json.dumps({"mode": "walk-only", "bucket": bool(args.bucket), "lattice": n,
+    print(json.dumps({"mode": "walk-only", "bucket": bool(args.bucket or args.pp),
+                      "pp": bool(args.pp), "lattice": n,
                       "receivers": A, "walk_ms": ms,
                       "units_per_s": A * npix * nb / (ms * 1e-3), "nodes": tree.n_nodes,
                       "max_depth": tree.max_depth}), flush=True)
@@ -621,6 +641,9 @@ def main():
     ap.add_argument("--lattice", type=int, default=128)
     ap.add_argument("--bucket", action="store_true",
                     help="with --walk-only: per-bucket beams (TREVR2_BUCKET)")
+    ap.add_argument("--pp", action="store_true",
+                    help="with --walk-only: per-bucket beams with p-p absorption and "
+                         "TREVR2_THICK")
     ap.add_argument("--no-bucket", action="store_true",
                     help="skip the per-bucket beams measurement")
     ap.add_argument("--no-batched", action="store_true",

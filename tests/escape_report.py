@@ -30,6 +30,8 @@ import workloads  # noqa: E402
 
 LINEAR = 8
 BUCKET = 16
+PP = 32
+THICK = 2
 NAMES = ["two_sources_cloud", "source_two_clouds", "source_wall"]
 
 
@@ -91,7 +93,10 @@ def main():
         gas_d = torch.as_tensor(gas, device="cuda")
         for method, flags in (("transmission", 0), ("linear", LINEAR),
                               ("transmission, per bucket", BUCKET),
-                              ("linear, per bucket", BUCKET | LINEAR)):
+                              ("linear, per bucket", BUCKET | LINEAR),
+                              ("transmission, per bucket, p-p, thick", BUCKET | PP | THICK),
+                              ("linear, per bucket, p-p, thick",
+                               BUCKET | PP | THICK | LINEAR)):
             J = tree.J(act_d, case["nside"], case["theta"], flags=flags).cpu().numpy()[:, 0]
             e, c = esc.figures(J, pts, g)
             e_o, c_o = esc.figures(ot.J(act, case["nside"], case["theta"], flags=flags)[:, 0],

@@ -8,7 +8,8 @@ clouds, a source beside a wall) are checked three ways:
   * the exact figures of merit against the "Exact" rows of Table escape,
     which fixes the reading of each geometry from the text;
   * the oracle's TREVR2 (transmission and linear averaging, with
-    per-receiver and with per-bucket beams) against the table's TREVR2 rows.
+    per-receiver beams, per-bucket beams, and per-bucket beams with p-p
+    absorption and Eq. taucorr) against the table's TREVR2 rows.
     Those rows come from a glass; here a jittered lattice stands in, so the
     bands are
     those that separate the table's methods from one another (a few tenths
@@ -26,6 +27,8 @@ import workloads
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 LINEAR = 8
 BUCKET = 16
+PP = 32
+THICK = 2
 
 
 def _table():
@@ -175,23 +178,26 @@ def oracle_figures(oracle_mod, esc):
         ot = oracle_mod.OracleTree.from_case(case)
         pts = case["pos"][case["active"]]
         for method, flags in (("transmission", 0), ("linear", LINEAR)):
-            for walk, wflag in (("receiver", 0), ("bucket", BUCKET)):
+            for walk, wflag in (("receiver", 0), ("bucket", BUCKET),
+                                ("bucket+pp+thick", BUCKET | PP | THICK)):
                 J = ot.J(case["active"], case["nside"], case["theta"], flags=flags | wflag)[:, 0]
                 out[(name, method, walk)] = esc.figures(J, pts, case["geometry"])
     return out
 
 
-@pytest.mark.parametrize("walk", ["receiver", "bucket"])
+@pytest.mark.parametrize("walk", ["receiver", "bucket", "bucket+pp+thick"])
 @pytest.mark.parametrize("key", sorted(BANDS))
 def test_oracle_matches_table_rows(oracle_figures, key, walk):
-    """Per-receiver beams and the paper's own per-bucket beams alike."""
+    """Per-receiver beams, the paper's per-bucket beams, and its full near
+    field (p-p absorption inside r_pp, with the receiver's own column by
+    Eq. taucorr) alike."""
     e, c = oracle_figures[key + (walk,)]
     want = _table()[key]
     de, dc = BANDS[key]
     assert abs(e - want[0]) <= de and abs(c - want[1]) <= dc, (key, e, c, want)
 
 
-@pytest.mark.parametrize("walk", ["receiver", "bucket"])
+@pytest.mark.parametrize("walk", ["receiver", "bucket", "bucket+pp+thick"])
 def test_linear_average_fails_on_the_combined_cloud(oracle_figures, walk):
     """Sec. 3.3: once the sources and the dense cloud share a cell the
     linear average wipes out most of the flux at r = 6 (the table prints
