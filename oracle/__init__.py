@@ -87,6 +87,8 @@ def _load():
         lib.oracle_cell_opens.argtypes = [P, P, P, P, f64, P]
         lib.oracle_beam_tau.restype = f64
         lib.oracle_beam_tau.argtypes = [P, i64, i32, f64, i64, f64, i32]
+        lib.oracle_J_directed.restype = i32
+        lib.oracle_J_directed.argtypes = [P, P, i64, i32, f64, u32, P, P, i32]
         lib.oracle_pp_sphere.restype = i64
         lib.oracle_pp_sphere.argtypes = [P, i64, i32, P, P]
         _lib = lib
@@ -227,10 +229,17 @@ class OracleTree:
             raise ValueError("bad nside")
         return out
 
-    def J(self, active, nside, theta, flags=0, nthreads=0, stats=False):
+    def J(self, active, nside, theta, flags=0, nthreads=0, stats=False, target=None):
         active = np.ascontiguousarray(np.asarray(active, dtype=np.int64))
         a = active.shape[0]
         J = np.zeros((a, self.nb))
+        if target is not None:  # directed rays (needs FLAG_BUCKET)
+            tg = _f64(target, (3,))
+            rc = _load().oracle_J_directed(self._h, _p(active), a, int(nside), float(theta),
+                                           int(flags), _p(tg), _p(J), int(nthreads))
+            if rc != 0:
+                raise ValueError("oracle_J_directed rejected its inputs")
+            return J
         st = np.zeros((a, 4), dtype=np.int64) if stats else None
         rc = _load().oracle_J(self._h, _p(active), a, int(nside), float(theta), int(flags),
                               _p(J), int(nthreads), _p(st))

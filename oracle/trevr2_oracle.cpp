@@ -62,6 +62,12 @@
 //     source than the receiver is and lies within h_j of the receiver-source
 //     segment (distance b) adds kappa_j Sigma_j(b), Sigma_j(b) =
 //     3 m_j / (pi h_j^2) (1 - b / h_j), whose area integral over b < h_j is m_j.
+//  R12 Directed rays (with FLAG_BUCKET; Sec. 3.4.1): given a target point,
+//     the beam that holds the target's direction from the bucket centre is
+//     aimed at the target instead of along its pixel centre; it keeps its
+//     pixel's direction pair for the cells' absorption, and the sources
+//     binned into it take their projected distance along the new direction.
+//     A target at the bucket centre leaves every beam as it is.
 
 #include <algorithm>
 #include <atomic>
@@ -586,6 +592,8 @@ struct Problem {
   std::vector<double> dirs;   // [npix][3]
   std::vector<int64_t> pair;  // [npix]
   std::vector<int64_t> leaf_of;  // [N] original index -> its leaf (FLAG_BUCKET)
+  bool directed = false;         // R12: aim one beam at `target`
+  double target[3] = {0, 0, 0};
   std::vector<double> pp_r;                  // [nodes] r_pp of each leaf (FLAG_PP)
   std::vector<std::vector<int64_t>> pp_list; // [nodes] its p-p particles (original)
 };
@@ -641,6 +649,23 @@ void walk_receiver(const Problem<T>& pr, int64_t i_orig, T* Jout, WalkStats* st)
   const bool pp = (pr.flags & FLAG_PP) != 0;
   const double rpp = pp ? pr.pp_r[pr.leaf_of[i_orig]] : 0.0;
   const std::vector<int64_t>* pplist = pp ? &pr.pp_list[pr.leaf_of[i_orig]] : nullptr;
+  // R12: the beam holding the target's direction points at the target
+  std::vector<double> dirs_directed;
+  const double* dirs = pr.dirs.data();
+  if (pr.directed) {
+    double vt[3], nt = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      vt[a] = pr.target[a] - xo[a];
+      nt += vt[a] * vt[a];
+    }
+    nt = std::sqrt(nt);
+    if (nt > 0.0) {
+      const int64_t kt = vec2pix_ring(pr.nside, vt);
+      dirs_directed = pr.dirs;
+      for (int a = 0; a < 3; ++a) dirs_directed[3 * kt + a] = vt[a] / nt;
+      dirs = dirs_directed.data();
+    }
+  }
   struct CutCell {
     int64_t node;
     double lo[3], hi[3];
@@ -707,7 +732,7 @@ void walk_receiver(const Problem<T>& pr, int64_t i_orig, T* Jout, WalkStats* st)
   };
   std::vector<std::vector<Seg>> segs(npix);
   for (int64_t k = 0; k < npix; ++k) {
-    const double* nk = &pr.dirs[3 * k];
+    const double* nk = &dirs[3 * k];
     for (const CutCell& cc : cut) {
       double t0, t1;
       if (!ray_chord(xo, nk, cc.lo, cc.hi, t0, t1)) continue;
@@ -731,7 +756,7 @@ void walk_receiver(const Problem<T>& pr, int64_t i_orig, T* Jout, WalkStats* st)
     if (val(vo[0]) == 0.0 && val(vo[1]) == 0.0 && val(vo[2]) == 0.0) continue;
     double vv[3] = {val(vo[0]), val(vo[1]), val(vo[2])};
     int64_t k = vec2pix_ring(pr.nside, vv);
-    const double* nk = &pr.dirs[3 * k];
+    const double* nk = &dirs[3 * k];
     T sp = vo[0] * nk[0] + vo[1] * nk[1] + vo[2] * nk[2];
     if (!(val(sp) > 0.0)) continue;  // cannot happen: beam radius < 90 degrees
     T v[3] = {s.p[0] - xi[0], s.p[1] - xi[1], s.p[2] - xi[2]};
@@ -1049,6 +1074,27 @@ int oracle_J(void* h, const int64_t* active, int64_t A, int nside, double theta,
       stats[4 * a + 2] = ws.segments;
       stats[4 * a + 3] = ws.sources;
     }
+  });
+  return 0;
+}
+
+// J with directed rays (R12): the per-bucket walk (flags must hold
+// FLAG_BUCKET) with the beam holding target[3] aimed at it.  Returns 0 or -1.
+int oracle_J_directed(void* h, const int64_t* active, int64_t A, int nside, double theta,
+                      uint32_t flags, const double* target, double* J, int nthreads) {
+  if (!valid_nside(nside) || !(theta > 0.0) || !(flags & FLAG_BUCKET)) return -1;
+  OracleTree& ot = *static_cast<OracleTree*>(h);
+  for (int64_t a = 0; a < A; ++a)
+    if (active[a] < 0 || active[a] >= ot.t.N) return -1;
+  ensure_table(ot, nside, (flags & FLAG_LINEAR) != 0);
+  Problem<double> pr = make_problem<double>(ot.t, ot.ag, ot.tab, ot.t.kappa, ot.t.lum, nside,
+                                            theta, flags);
+  pr.directed = true;
+  for (int a = 0; a < 3; ++a) pr.target[a] = target[a];
+  prepare_pp(pr, active, A, nthreads);
+  const int nb = ot.t.nb;
+  parallel_for(A, nthreads, [&](int64_t a) {
+    walk_receiver<double>(pr, active[a], &J[a * nb], nullptr);
   });
   return 0;
 }

@@ -872,3 +872,70 @@ def test_pp_needs_bucket(oracle_mod):
     t = oracle_mod.OracleTree.from_case(case)
     with pytest.raises(ValueError):
         t.J(case["active"], 2, 0.75, flags=oracle_mod.FLAG_PP)
+
+
+# ----------------------------------------------------------------------------
+# Directed rays (Sec. 3.4.1, with per-bucket beams): the beam that holds the
+# target's direction points at the target.
+
+def _leaf_alpha_along(e, ag, a, b, m=200_000, band=0):
+    """Line integral of the leaves' bucket absorption from a to b, by point
+    sampling (the cut at theta -> 0 is every leaf)."""
+    ts = (np.arange(m) + 0.5) / m
+    pts = a[None, :] + ts[:, None] * (b - a)[None, :]
+    node = np.zeros(m, dtype=np.int64)
+    while True:
+        internal = e["child"][node] >= 0
+        if not internal.any():
+            break
+        idx = np.flatnonzero(internal)
+        q = node[idx]
+        ax = e["depth"][q] % 3
+        mid = 0.5 * (e["box"][q, ax] + e["box"][q, 3 + ax])
+        node[idx] = e["child"][q] + (pts[idx, ax] >= mid).astype(np.int64)
+    return ag["alpha_leaf"][node, band].sum() * np.linalg.norm(b - a) / m
+
+
+def test_directed_beam_is_the_line_to_the_target(oracle_mod):
+    """theta -> 0, one star as the target: every receiver's optical depth per
+    unit distance, -ln(4 pi r^2 J / L) / r, is the line integral of the
+    leaves' absorption from its bucket centre straight to the star over the
+    centre's distance s; the pixel-centre beam gives something else."""
+    case = workloads.random_case(500, 1, nb=1, seed=141, clumped=True, kappa_scale=20.0)
+    n = len(case["pos"])
+    case["active"] = np.arange(n - 1)
+    star = case["pos"][-1]
+    t = oracle_mod.OracleTree.from_case(case)
+    e, ag = t.export(), t.aggregates()
+    centres = _leaf_centres(t, n)
+    L = float(case["lum"][-1, 0])
+    rng = np.random.default_rng(2)
+    act = rng.choice(n - 1, 25, replace=False)
+    flags = oracle_mod.FLAG_BUCKET
+    Jd = t.J(act, 2, 1e-9, flags=flags, target=star)[:, 0]
+    Jp = t.J(act, 2, 1e-9, flags=flags)[:, 0]
+    r = np.linalg.norm(case["pos"][act] - star, axis=1)
+    differs = 0
+    for a, i in enumerate(act):
+        s = np.linalg.norm(star - centres[i])
+        want = _leaf_alpha_along(e, ag, centres[i], star) / s
+        got = -np.log(4 * np.pi * r[a] ** 2 * Jd[a] / L) / r[a]
+        assert got == pytest.approx(want, rel=2e-3, abs=1e-9)
+        differs += abs(-np.log(4 * np.pi * r[a] ** 2 * Jp[a] / L) / r[a] - want) > 1e-2 * want
+    assert differs > 0
+
+
+def test_directed_needs_bucket_and_keeps_closed_form(oracle_mod):
+    case = workloads.uniform_point_source(offset=True)
+    t = oracle_mod.OracleTree.from_case(case)
+    src = case["pos"][-1]
+    with pytest.raises(ValueError):
+        t.J(case["active"][:5], 2, 0.75, target=src)
+    J = t.J(case["active"], 2, 0.75, flags=oracle_mod.FLAG_BUCKET, target=src)
+    r = np.linalg.norm(case["pos"][case["active"]] - src, axis=1)
+    # the directed beam runs from each bucket centre straight to the source:
+    # kappa rho s along it, times r/s, whatever the cut
+    centres = _leaf_centres(t, len(case["pos"]))[case["active"]]
+    ok = np.all((centres >= 0) & (centres < 1), axis=1)
+    np.testing.assert_allclose(J[ok, 0], np.exp(-2.0 * r[ok]) / (4 * np.pi * r[ok] ** 2),
+                               rtol=1e-12)
