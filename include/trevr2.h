@@ -136,6 +136,24 @@ int trevr2_J(trevr2_tree* tree, const int64_t* active, int64_t A, int nside, flo
              const int* bands, int nbsel, uint32_t flags, float* J, void* stream);
 
 /*
+ * trevr2_J_directed — trevr2_J with one beam aimed at a target (Sec. 3.4.1:
+ * for a single-source test the beam is pointed at the source instead of along
+ * the centre of its HEALPix pixel).  Per bucket, the beam whose pixel holds
+ * the direction from the bucket centre to `target` takes that exact
+ * direction; it keeps its pixel's direction pair for the cells' absorption,
+ * and the sources binned into it take their projected distance along it.
+ * A target at a bucket centre leaves that bucket's beams as they are.
+ *
+ *  target  host [3] float64 point in the caller's coordinates
+ * The other arguments, the output and the errors are those of trevr2_J;
+ * flags must include TREVR2_BUCKET (else EINVAL), as must a NULL or
+ * non-finite target.
+ */
+int trevr2_J_directed(trevr2_tree* tree, const int64_t* active, int64_t A, int nside, float theta,
+                      const int* bands, int nbsel, uint32_t flags, const double* target,
+                      float* J, void* stream);
+
+/*
  * trevr2_prepare — builds and caches the per-direction absorption tables of
  * Eq. transmissionavg (Sec. 2.6; N_ray/2 values per cell and band) and the
  * HEALPix beam table for `nside`, without running a walk.  trevr2_J does the

@@ -102,6 +102,7 @@ def load_library():
                                           C.c_uint32, C.c_size_t)
         lib.trevr2_build.argtypes = [P, P, P, P, P, i64, i32, P, f64, i32, P, C.POINTER(P)]
         lib.trevr2_J.argtypes = [P, P, i64, i32, f32, P, i32, u32, P, P]
+        lib.trevr2_J_directed.argtypes = [P, P, i64, i32, f32, P, i32, u32, P, P, P]
         lib.trevr2_status.argtypes = [P, P]
         lib.trevr2_prepare.argtypes = [P, i32, P]
         lib.trevr2_J_noalloc.argtypes = [P, P, i64, i32, f32, P, i32, u32, P, P]
@@ -180,8 +181,11 @@ class Tree:
 
     # -- compute -------------------------------------------------------------
     def J(self, active, nside: int = 2, theta: float = 0.75, bands=None, flags: int = 0,
-          out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-        """Integrated intensity per active receiver and band, [A, nbsel] float32."""
+          out: torch.Tensor | None = None, stream=None, target=None) -> torch.Tensor:
+        """Integrated intensity per active receiver and band, [A, nbsel] float32.
+        With `target` (a point, caller coordinates; needs BUCKET) the beam that
+        holds the target's direction from each bucket centre points at it
+        (directed rays, Sec. 3.4.1)."""
         self._alive()
         act = _dev(active, torch.int64, self.device).reshape(-1)
         nbsel = self.nb if bands is None else len(bands)
@@ -190,6 +194,12 @@ class Tree:
         barr = None
         if bands is not None:
             barr = (C.c_int * len(bands))(*[int(b) for b in bands])
+        if target is not None:
+            tg = (C.c_double * 3)(*[float(v) for v in np.asarray(target, dtype=np.float64).reshape(3)])
+            _check(load_library().trevr2_J_directed(self._h, _ptr(act), act.numel(), int(nside),
+                                                    float(theta), barr, int(nbsel), int(flags),
+                                                    tg, _ptr(out), _stream_ptr(stream)))
+            return out
         _check(load_library().trevr2_J(self._h, _ptr(act), act.numel(), int(nside), float(theta),
                                        barr, int(nbsel), int(flags), _ptr(out),
                                        _stream_ptr(stream)))

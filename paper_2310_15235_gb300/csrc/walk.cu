@@ -56,7 +56,11 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
     const int end = off[k];
     const float smax = V[end - 1].s;
     float s_next = V[ptr].s;  // the nearest source not yet passed
-    const float4 dn = a.dirs[k];
+    float4 dn = a.dirs[k];
+    if constexpr (kBucket) {  // the directed beam (Sec. 3.4.1) points at its target
+      const double* o = origin64<true>(a, si);
+      if (int(o[7]) == k) dn = make_float4(float(o[4]), float(o[5]), float(o[6]), dn.w);
+    }
     const int pair = __float_as_int(dn.w);
     const float n[3] = {dn.x, dn.y, dn.z};
     float inv[3];
@@ -280,6 +284,9 @@ struct BucketArgs {
   float4* pp_kc;         // [warps][pp_cap] kappa_b m 3 / (pi h^2) per band
   int* pp_si;            // [warps][pp_cap] sorted element index
   float4* pp_w;          // [warps][pp_cap] per receiver: x_k - x, |x_k - x|^2 - h_k^2
+  // directed rays (Sec. 3.4.1): the beam holding the target points at it
+  int directed;
+  double target[3];      // normalised
 };
 
 // The leaf holding each slot's element: down the tree by the first element
@@ -551,10 +558,23 @@ __device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0,
   const float3 o = make_float3(lf.lo[0] + 0.5f * e.x, lf.lo[1] + 0.5f * e.y, lf.lo[2] + 0.5f * e.z);
   const int si_o = int(-1 - gw);  // the warp's origin slot (origin64<true>)
   if (lane == 0) {
-    double* o64 = a.origin64 + 4 * gw;
+    double* o64 = a.origin64 + kOriginWords * gw;
     o64[0] = double(o.x);
     o64[1] = double(o.y);
     o64[2] = double(o.z);
+    o64[3] = 0.0;
+    o64[7] = -1.0;
+    if (bk.directed) {  // Sec. 3.4.1: the beam holding the target points at it
+      const double vx = bk.target[0] - o64[0], vy = bk.target[1] - o64[1],
+                   vz = bk.target[2] - o64[2];
+      const double nv = sqrt(vx * vx + vy * vy + vz * vz);
+      if (nv > 0.0) {
+        o64[4] = vx / nv;
+        o64[5] = vy / nv;
+        o64[6] = vz / nv;
+        o64[7] = double(hp_vec2pix_f64(a.nside, vx, vy, vz));
+      }
+    }
   }
   NodeW* chain = reinterpret_cast<NodeW*>(off + 2 * a.npix + 36);
   const int leaf = build_chain(a.nodes, o, lane, chain);  // == q
@@ -566,8 +586,8 @@ __device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0,
     const double r0 = 0.5 * sqrt(double(e.x) * e.x + double(e.y) * e.y + double(e.z) * e.z);
     double r64 = 0.0;
     __syncwarp();
-    npp = collect_pp<NBP>(a, bk, a.origin64 + 4 * gw, r0, lane, stk, gw, r64);
-    if (lane == 0) a.origin64[4 * gw + 3] = r64;
+    npp = collect_pp<NBP>(a, bk, a.origin64 + kOriginWords * gw, r0, lane, stk, gw, r64);
+    if (lane == 0) a.origin64[kOriginWords * gw + 3] = r64;
     rpp = float(r64);
     __syncwarp();
   }
@@ -955,7 +975,7 @@ constexpr int kPPCapacity = 4096;
 // bucket.
 static int launch_walk_bucket(Tree* t, Table* tb, const int64_t* active, int64_t A, int nside,
                               float theta, const int* bsel, int nbsel, uint32_t flags, float* J,
-                              cudaStream_t st) {
+                              const double* target, cudaStream_t st) {
   WalkArgs a;
   // the walk from the bucket centre takes no receiver flags; they go to bk
   fill_walk_args(t, tb, nside, theta, bsel, nbsel, flags & ~(TREVR2_SOFT | TREVR2_THICK),
@@ -995,6 +1015,8 @@ static int launch_walk_bucket(Tree* t, Table* tb, const int64_t* active, int64_t
   bk.pp_cap = bk.pp ? kPPCapacity : 0;
   bk.beam = std::sqrt(4.0 * M_PI / double(a.npix));
   bk.mass = t->mass;
+  bk.directed = target != nullptr;
+  for (int c = 0; c < 3; ++c) bk.target[c] = target ? (target[c] - t->lo[c]) / t->size : 0.0;
   const void* fn = t->nbp == 1 ? bucket_kernel_nbp<1>(bk.pp)
                  : t->nbp == 2 ? bucket_kernel_nbp<2>(bk.pp) : bucket_kernel_nbp<4>(bk.pp);
   const size_t smem = walk_smem(kWalkWarps, a.stack_ints, a.npix, a.max_depth);
@@ -1005,7 +1027,7 @@ static int launch_walk_bucket(Tree* t, Table* tb, const int64_t* active, int64_t
   blocks = std::max<int64_t>(blocks, 1);
   const size_t warps = size_t(blocks) * kWalkWarps;
   const size_t wb = (walk_buffer_bytes(warps, a.M) + 255) & ~size_t(255);
-  const size_t ob = (warps * 4 * sizeof(double) + 255) & ~size_t(255);
+  const size_t ob = (warps * kOriginWords * sizeof(double) + 255) & ~size_t(255);
   const size_t pb = warps * size_t(bk.pp_cap) * (3 * sizeof(float4) + sizeof(int));
   const size_t need = wb + ob + pb;
   if (t->scratch_bytes < need) {
@@ -1059,12 +1081,26 @@ int read_status(Tree* t, cudaStream_t st) {
 
 using namespace trevr2;
 
-extern "C" int trevr2_J(trevr2_tree* tree, const int64_t* active, int64_t A, int nside, float theta,
-                        const int* bands, int nbsel, uint32_t flags, float* J, void* stream) {
+// trevr2_J and trevr2_J_directed (target != NULL).
+static int J_impl(trevr2_tree* tree, const int64_t* active, int64_t A, int nside, float theta,
+                  const int* bands, int nbsel, uint32_t flags, const double* target, float* J,
+                  void* stream) {
   clear_error();
   if (!tree) {
     set_error("trevr2_J: tree is NULL");
     return TREVR2_EINVAL;
+  }
+  if (target) {
+    if (!(flags & TREVR2_BUCKET)) {
+      set_error("trevr2_J_directed: directed rays need TREVR2_BUCKET");
+      return TREVR2_EINVAL;
+    }
+    for (int c = 0; c < 3; ++c) {
+      if (!std::isfinite(target[c])) {
+        set_error("trevr2_J_directed: the target is not finite");
+        return TREVR2_EINVAL;
+      }
+    }
   }
   Tree* t = reinterpret_cast<Tree*>(tree);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1111,11 +1147,28 @@ extern "C" int trevr2_J(trevr2_tree* tree, const int64_t* active, int64_t A, int
   Table* tb = nullptr;
   T2_CHECK(ensure_table(t, nside, st, &tb, (flags & TREVR2_LINEAR) != 0));
   if (flags & TREVR2_BUCKET)
-    T2_CHECK(launch_walk_bucket(t, tb, active, A, nside, theta, bsel, nbsel, flags, J, st));
+    T2_CHECK(launch_walk_bucket(t, tb, active, A, nside, theta, bsel, nbsel, flags, J, target,
+                                st));
   else
     T2_CHECK(launch_walk(t, tb, active, A, nside, theta, bsel, nbsel, flags, J, st));
   if (flags & TREVR2_ASYNC) return TREVR2_OK;
   return read_status(t, st);
+}
+
+extern "C" int trevr2_J(trevr2_tree* tree, const int64_t* active, int64_t A, int nside, float theta,
+                        const int* bands, int nbsel, uint32_t flags, float* J, void* stream) {
+  return J_impl(tree, active, A, nside, theta, bands, nbsel, flags, nullptr, J, stream);
+}
+
+extern "C" int trevr2_J_directed(trevr2_tree* tree, const int64_t* active, int64_t A, int nside,
+                                 float theta, const int* bands, int nbsel, uint32_t flags,
+                                 const double* target, float* J, void* stream) {
+  if (!target) {
+    clear_error();
+    set_error("trevr2_J_directed: target is NULL");
+    return TREVR2_EINVAL;
+  }
+  return J_impl(tree, active, A, nside, theta, bands, nbsel, flags, target, J, stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -53,7 +53,8 @@ struct WalkArgs {
   int* pixU;
   SrcEntry* srcV;
   float* srcT;      // [warps][M][4] optical depth tau_k(s) of every staged source
-  double* origin64; // [warps][4] FP64 bucket centre of each warp (per-bucket walk)
+  double* origin64; // [warps][kOriginWords] per-bucket walk: FP64 centre, r_pp,
+                    // directed beam (unit vector, pixel or -1)
   int M;
   int stack_ints;   // per warp
   int max_depth;
@@ -193,11 +194,16 @@ __device__ __forceinline__ float3 grazing_coords(const WalkArgs& a, int si, floa
   return make_float3(g[0], g[1], g[2]);
 }
 
+// The per-bucket walk's slot of warp w: [0..2] FP64 bucket centre, [3] FP64
+// p-p radius, [4..6] unit vector of the directed beam, [7] its pixel (-1:
+// none).
+constexpr int kOriginWords = 8;
+
 // The FP64 origin of a walk: the receiver's FP64 position, or (kBucket) the
-// bucket centre that warp w = -1 - si keeps in origin64[4 w ...].
+// bucket centre in the slot of warp w = -1 - si.
 template <bool kBucket>
 __device__ __forceinline__ const double* origin64(const WalkArgs& a, int si) {
-  if constexpr (kBucket) return a.origin64 + 4 * int64_t(-1 - si);
+  if constexpr (kBucket) return a.origin64 + kOriginWords * int64_t(-1 - si);
   return a.pos64 + 3 * int64_t(si);
 }
 
@@ -291,7 +297,11 @@ __device__ __forceinline__ bool make_source(const WalkArgs& a, float3 p, const d
     k = hp_vec2pix_f64(a.nside, __dsub_rn(p64[0], x64[0]), __dsub_rn(p64[1], x64[1]),
                        __dsub_rn(p64[2], x64[2]));
   }
-  const float4 n = a.dirs[k];
+  float4 n = a.dirs[k];
+  if constexpr (kBucket) {  // the directed beam (Sec. 3.4.1) points at its target
+    const double* o = origin64<true>(a, si);
+    if (int(o[7]) == k) n = make_float4(float(o[4]), float(o[5]), float(o[6]), n.w);
+  }
   const float s = vx * n.x + vy * n.y + vz * n.z;
   if (!(s > 0.0f)) return false;
   out.s = s;

@@ -91,18 +91,25 @@ def main():
         e_x, c_x = esc.figures(esc.exact_J(pts, g), pts, g)
         act_d = torch.as_tensor(act, device="cuda")
         gas_d = torch.as_tensor(gas, device="cuda")
-        for method, flags in (("transmission", 0), ("linear", LINEAR),
-                              ("transmission, per bucket", BUCKET),
-                              ("linear, per bucket", BUCKET | LINEAR),
-                              ("transmission, per bucket, p-p, thick", BUCKET | PP | THICK),
-                              ("linear, per bucket, p-p, thick",
-                               BUCKET | PP | THICK | LINEAR)):
-            J = tree.J(act_d, case["nside"], case["theta"], flags=flags).cpu().numpy()[:, 0]
+        methods = [("transmission", 0), ("linear", LINEAR),
+                   ("transmission, per bucket", BUCKET),
+                   ("linear, per bucket", BUCKET | LINEAR),
+                   ("transmission, per bucket, p-p, thick", BUCKET | PP | THICK),
+                   ("linear, per bucket, p-p, thick", BUCKET | PP | THICK | LINEAR)]
+        if len(g["sources"]) == 1:  # directed rays aim at the one source
+            methods += [("directed, per bucket", BUCKET),
+                        ("directed, per bucket, p-p, thick", BUCKET | PP | THICK)]
+        for method, flags in methods:
+            tg = g["sources"][0] if "directed" in method else None
+            J = tree.J(act_d, case["nside"], case["theta"], flags=flags,
+                       target=tg).cpu().numpy()[:, 0]
             e, c = esc.figures(J, pts, g)
-            e_o, c_o = esc.figures(ot.J(act, case["nside"], case["theta"], flags=flags)[:, 0],
-                                   pts, g)
-            t_shell = _time(lambda: tree.J(act_d, case["nside"], case["theta"], flags=flags))
-            t_all = _time(lambda: tree.J(gas_d, case["nside"], case["theta"], flags=flags))
+            e_o, c_o = esc.figures(ot.J(act, case["nside"], case["theta"], flags=flags,
+                                        target=tg)[:, 0], pts, g)
+            t_shell = _time(lambda: tree.J(act_d, case["nside"], case["theta"], flags=flags,
+                                           target=tg))
+            t_all = _time(lambda: tree.J(gas_d, case["nside"], case["theta"], flags=flags,
+                                         target=tg))
             # the paper's rows come from its per-bucket walk; both are shown
             paper = table.get((name, method.split(",")[0]), (float("nan"), float("nan")))
             rows.append(dict(test=name, method=method, elements=len(case["pos"]),

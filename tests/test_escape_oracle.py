@@ -197,6 +197,24 @@ def test_oracle_matches_table_rows(oracle_figures, key, walk):
     assert abs(e - want[0]) <= de and abs(c - want[1]) <= dc, (key, e, c, want)
 
 
+DIRECTED_BANDS = {"source_two_clouds": (0.003, 0.005), "source_wall": (0.003, 0.03)}
+
+
+@pytest.mark.parametrize("name", sorted(DIRECTED_BANDS))
+def test_directed_rows(oracle_mod, esc, name):
+    """The table's "Directed" rows (Sec. 3.4.1): the per-bucket walk with the
+    beam holding the source aimed at it."""
+    case = workloads.CASES[name]()
+    g = case["geometry"]
+    ot = oracle_mod.OracleTree.from_case(case)
+    J = ot.J(case["active"], case["nside"], case["theta"], flags=BUCKET,
+             target=g["sources"][0])[:, 0]
+    e, c = esc.figures(J, case["pos"][case["active"]], g)
+    want = _table()[(name, "directed")]
+    de, dc = DIRECTED_BANDS[name]
+    assert abs(e - want[0]) <= de and abs(c - want[1]) <= dc, (name, e, c, want)
+
+
 @pytest.mark.parametrize("walk", ["receiver", "bucket", "bucket+pp+thick"])
 def test_linear_average_fails_on_the_combined_cloud(oracle_figures, walk):
     """Sec. 3.3: once the sources and the dense cloud share a cell the
