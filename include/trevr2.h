@@ -154,6 +154,24 @@ int trevr2_J_directed(trevr2_tree* tree, const int64_t* active, int64_t A, int n
                       float* J, void* stream);
 
 /*
+ * trevr2_set_tau_refine — absorption refinement (Sec. 2.5.2, the TREVR
+ * criterion the paper keeps as an option, off by default): every later walk
+ * on this tree also opens a cell whose optical depth varies by more than
+ * tau_refine inside it, the variation being (largest - smallest bucket alpha
+ * among the leaves under the cell, per band) times the cell's longest side,
+ * the largest over the bands.  Leaves do not open further.  Applies to
+ * trevr2_J, trevr2_J_directed, trevr2_J_noalloc and trevr2_J_backward, and
+ * to batch plans created while it is on (they read the tree's refined node
+ * copy when they run; create plans after setting it).
+ *
+ *  tau_refine  > 0; +infinity turns refinement off (the default)
+ * The first call allocates the per-cell variation and a copy of the node
+ * records (freed by trevr2_free).  Stream ordered, does not synchronise.
+ * Errors: EINVAL (NULL tree, tau_refine <= 0 or NaN), ENOMEM, ECUDA.
+ */
+int trevr2_set_tau_refine(trevr2_tree* tree, double tau_refine, void* stream);
+
+/*
  * trevr2_prepare — builds and caches the per-direction absorption tables of
  * Eq. transmissionavg (Sec. 2.6; N_ray/2 values per cell and band) and the
  * HEALPix beam table for `nside`, without running a walk.  trevr2_J does the

@@ -89,6 +89,8 @@ def _load():
         lib.oracle_beam_tau.argtypes = [P, i64, i32, f64, i64, f64, i32]
         lib.oracle_J_directed.restype = i32
         lib.oracle_J_directed.argtypes = [P, P, i64, i32, f64, u32, P, P, i32]
+        lib.oracle_set_tau_refine.restype = i32
+        lib.oracle_set_tau_refine.argtypes = [P, f64, P]
         lib.oracle_pp_sphere.restype = i64
         lib.oracle_pp_sphere.argtypes = [P, i64, i32, P, P]
         _lib = lib
@@ -251,6 +253,14 @@ class OracleTree:
         """Optical depth along beam k of receiver i up to distance s (no r/s)."""
         return _load().oracle_beam_tau(self._h, int(i), int(nside), float(theta), int(k),
                                        float(s), int(band))
+
+    def set_tau_refine(self, tau_refine):
+        """Refinement for every later call (R13; inf turns it off); returns the
+        per-node optical-depth variation it compares with tau_refine."""
+        out = np.empty(self.num_nodes)
+        if _load().oracle_set_tau_refine(self._h, float(tau_refine), _p(out)) != 0:
+            raise ValueError("tau_refine must be positive")
+        return out
 
     def pp_sphere(self, i, nside):
         """(r_pp, sorted original indices of the p-p particles) of the bucket

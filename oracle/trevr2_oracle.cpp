@@ -68,6 +68,11 @@
 //     pixel's direction pair for the cells' absorption, and the sources
 //     binned into it take their projected distance along the new direction.
 //     A target at the bucket centre leaves every beam as it is.
+//  R13 Refinement tau_refine (Sec. 2.5.2; off, i.e. infinite, by default):
+//     a cell whose optical depth varies by more than tau_refine inside it
+//     also opens.  The variation is read as (largest - smallest bucket alpha
+//     among the leaves under the cell) times the cell's longest side, the
+//     largest over the bands.  Leaves are buckets and never open further.
 
 #include <algorithm>
 #include <atomic>
@@ -594,6 +599,8 @@ struct Problem {
   std::vector<int64_t> leaf_of;  // [N] original index -> its leaf (FLAG_BUCKET)
   bool directed = false;         // R12: aim one beam at `target`
   double target[3] = {0, 0, 0};
+  double tau_refine = std::numeric_limits<double>::infinity();  // R13
+  const std::vector<double>* dtau = nullptr;                     // [nodes]
   std::vector<double> pp_r;                  // [nodes] r_pp of each leaf (FLAG_PP)
   std::vector<std::vector<int64_t>> pp_list; // [nodes] its p-p particles (original)
 };
@@ -695,7 +702,8 @@ void walk_receiver(const Problem<T>& pr, int64_t i_orig, T* Jout, WalkStats* st)
     node_box(nd, t.lo, t.size, cc.lo, cc.hi);
     ++ws.visited;
     bool open = cell_opens(xo, cc.lo, cc.hi, ag.B[q], pr.theta) ||
-                (pp && box_distance(xo, cc.lo, cc.hi) < rpp);
+                (pp && box_distance(xo, cc.lo, cc.hi) < rpp) ||
+                (pr.dtau && (*pr.dtau)[q] > pr.tau_refine);
     if (!open) {
       cut.push_back(cc);
       if (val(ag.Ltot[q]) > 0.0) {
@@ -899,7 +907,44 @@ struct OracleTree {
   std::vector<double> tab;
   int tab_nside = -1;
   bool tab_linear = false;
+  double tau_refine = std::numeric_limits<double>::infinity();  // R13
+  std::vector<double> dtau;                                      // [nodes]
 };
+
+// R13: the optical-depth variation inside every cell, from the leaves up
+// (children come after their parent in breadth-first order).
+std::vector<double> tau_variation(const Tree& t, const Aggregates<double>& ag) {
+  const int64_t n = static_cast<int64_t>(t.nodes.size());
+  const int nb = t.nb;
+  std::vector<double> amin(n * nb), amax(n * nb), out(n, 0.0);
+  for (int64_t q = n - 1; q >= 0; --q) {
+    const Node& nd = t.nodes[q];
+    for (int b = 0; b < nb; ++b) {
+      if (nd.child < 0) {
+        amin[q * nb + b] = amax[q * nb + b] = ag.alpha[q * nb + b];
+      } else {
+        const int64_t c = nd.child;
+        amin[q * nb + b] = std::min(amin[c * nb + b], amin[(c + 1) * nb + b]);
+        amax[q * nb + b] = std::max(amax[c * nb + b], amax[(c + 1) * nb + b]);
+      }
+    }
+    double lo[3], hi[3], side = 0.0, var = 0.0;
+    node_box(nd, t.lo, t.size, lo, hi);
+    for (int a = 0; a < 3; ++a) side = std::max(side, hi[a] - lo[a]);
+    for (int b = 0; b < nb; ++b) var = std::max(var, amax[q * nb + b] - amin[q * nb + b]);
+    out[q] = var * side;
+  }
+  return out;
+}
+
+// Problems built from an oracle tree see its refinement setting.
+template <class T>
+void apply_refine(const OracleTree& ot, Problem<T>& pr) {
+  if (std::isfinite(ot.tau_refine)) {
+    pr.tau_refine = ot.tau_refine;
+    pr.dtau = &ot.dtau;
+  }
+}
 
 void ensure_table(OracleTree& ot, int nside, bool linear = false) {
   if (ot.tab_nside == nside && ot.tab_linear == linear) return;
@@ -1063,6 +1108,7 @@ int oracle_J(void* h, const int64_t* active, int64_t A, int nside, double theta,
   ensure_table(ot, nside, (flags & FLAG_LINEAR) != 0);
   Problem<double> pr = make_problem<double>(ot.t, ot.ag, ot.tab, ot.t.kappa, ot.t.lum, nside,
                                             theta, flags);
+  apply_refine(ot, pr);
   prepare_pp(pr, active, A, nthreads);
   const int nb = ot.t.nb;
   parallel_for(A, nthreads, [&](int64_t a) {
@@ -1089,6 +1135,7 @@ int oracle_J_directed(void* h, const int64_t* active, int64_t A, int nside, doub
   ensure_table(ot, nside, (flags & FLAG_LINEAR) != 0);
   Problem<double> pr = make_problem<double>(ot.t, ot.ag, ot.tab, ot.t.kappa, ot.t.lum, nside,
                                             theta, flags);
+  apply_refine(ot, pr);
   pr.directed = true;
   for (int a = 0; a < 3; ++a) pr.target[a] = target[a];
   prepare_pp(pr, active, A, nthreads);
@@ -1117,6 +1164,7 @@ int oracle_J_deriv(void* h, const int64_t* active, int64_t A, int nside, double 
   Aggregates<Dual> ag = compute_aggregates<Dual>(t, kappa, lum);
   std::vector<Dual> tab = alpha_tables<Dual>(t, ag, nside, (flags & FLAG_LINEAR) != 0);
   Problem<Dual> pr = make_problem<Dual>(t, ag, tab, kappa, lum, nside, theta, flags);
+  apply_refine(ot, pr);
   prepare_pp(pr, active, A, nthreads);
   parallel_for(A, nthreads, [&](int64_t a) {
     std::vector<Dual> Jd(nb);
@@ -1142,6 +1190,18 @@ int64_t oracle_pp_sphere(void* h, int64_t i, int nside, double* rpp, int64_t* li
   std::sort(l.begin(), l.end());
   if (list) std::copy(l.begin(), l.end(), list);
   return static_cast<int64_t>(l.size());
+}
+
+// R13: refinement for every later call; tau_refine <= 0 or NaN is
+// rejected (-1), +infinity turns it off.  dtau_out (may be NULL) receives
+// the per-node variation [nodes].
+int oracle_set_tau_refine(void* h, double tau_refine, double* dtau_out) {
+  OracleTree& ot = *static_cast<OracleTree*>(h);
+  if (!(tau_refine > 0.0)) return -1;
+  if (ot.dtau.empty()) ot.dtau = tau_variation(ot.t, ot.ag);
+  ot.tau_refine = tau_refine;
+  if (dtau_out) std::copy(ot.dtau.begin(), ot.dtau.end(), dtau_out);
+  return 0;
 }
 
 // Opening decision for one cell with the given centre of luminosity.
@@ -1174,7 +1234,8 @@ double oracle_beam_tau(void* h, int64_t i_orig, int nside, double theta, int64_t
     const Node& nd = t.nodes[q];
     double lo[3], hi[3];
     node_box(nd, t.lo, t.size, lo, hi);
-    bool open = cell_opens(xi, lo, hi, ot.ag.B[q], theta);
+    bool open = cell_opens(xi, lo, hi, ot.ag.B[q], theta) ||
+                (std::isfinite(ot.tau_refine) && ot.dtau[q] > ot.tau_refine);
     if (open && nd.child >= 0) {
       stack.push_back(nd.child + 1);
       stack.push_back(nd.child);

@@ -103,6 +103,7 @@ def load_library():
         lib.trevr2_build.argtypes = [P, P, P, P, P, i64, i32, P, f64, i32, P, C.POINTER(P)]
         lib.trevr2_J.argtypes = [P, P, i64, i32, f32, P, i32, u32, P, P]
         lib.trevr2_J_directed.argtypes = [P, P, i64, i32, f32, P, i32, u32, P, P, P]
+        lib.trevr2_set_tau_refine.argtypes = [P, C.c_double, P]
         lib.trevr2_status.argtypes = [P, P]
         lib.trevr2_prepare.argtypes = [P, i32, P]
         lib.trevr2_J_noalloc.argtypes = [P, P, i64, i32, f32, P, i32, u32, P, P]
@@ -222,6 +223,14 @@ class Tree:
                                                 float(theta), barr, int(nbsel), int(flags),
                                                 _ptr(g), _ptr(gk), _ptr(gl), _stream_ptr(stream)))
         return gk, gl
+
+    def set_tau_refine(self, tau_refine: float, stream=None):
+        """Absorption refinement for every later walk on this tree (Sec. 2.5.2):
+        cells whose optical depth varies by more than tau_refine inside also
+        open; float('inf') turns it off."""
+        self._alive()
+        _check(load_library().trevr2_set_tau_refine(self._h, float(tau_refine),
+                                                    _stream_ptr(stream)))
 
     def prepare(self, nside: int, stream=None):
         """Builds and caches the per-direction tables for `nside` (no walk)."""

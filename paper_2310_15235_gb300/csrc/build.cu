@@ -566,6 +566,8 @@ static void free_tree(Tree* t, cudaStream_t st) {
   dfree(t->c64, st);
   dfree(t->B64, st);
   dfree(t->alpha_leaf, st);
+  dfree(t->dtau, st);
+  dfree(t->nodes_refined, st);
   for (Table& tb : t->tables) {
     dfree(tb.alpha, st);
     dfree(tb.dirs, st);
@@ -952,5 +954,106 @@ extern "C" int trevr2_tree_export(const trevr2_tree* tree, int field, void* dst,
                                                        static_cast<double*>(dst)); note_launch();
   }
   T2_CUDA(cudaGetLastError());
+  return TREVR2_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Refinement tau_refine (Sec. 2.5.2; off by default): a cell whose optical
+// depth varies by more than tau_refine inside it opens as well.  The
+// variation is (largest - smallest bucket alpha among the leaves under the
+// cell) times its longest side, the largest over the bands.  Opening is
+// forced by a node copy whose B is so large that B > theta d holds for
+// every d in the unit cube, so every walk (forward, per bucket, batched,
+// adjoint) refines without any change to its code.
+namespace trevr2 {
+
+constexpr float kRefinedB = 1e18f;  // B^2 and the FP32 guard stay finite
+
+// One depth of the tree, deepest first: the per-band range of the leaves'
+// alpha under each node and the node's variation.
+template <int NBP>
+__global__ void k_tau_variation_level(int64_t lb, int64_t le, const NodeW* __restrict__ nodes,
+                                      const float* __restrict__ alpha_leaf, float* amin,
+                                      float* amax, float* __restrict__ dtau) {
+  const int64_t q = lb + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q >= le) return;
+  const NodeW nd = nodes[q];
+  float var = 0.0f;
+#pragma unroll
+  for (int b = 0; b < NBP; ++b) {
+    float lo, hi;
+    if (nd.meta & kMetaLeaf) {
+      lo = hi = alpha_leaf[q * NBP + b];
+    } else {
+      const int64_t c = nd.child;
+      lo = fminf(amin[c * NBP + b], amin[(c + 1) * NBP + b]);
+      hi = fmaxf(amax[c * NBP + b], amax[(c + 1) * NBP + b]);
+    }
+    amin[q * NBP + b] = lo;
+    amax[q * NBP + b] = hi;
+    var = fmaxf(var, hi - lo);
+  }
+  // the longest side: the axis split least often, z, floor(depth / 3) times
+  const int d = int(nd.meta & kMetaDepthMask);
+  dtau[q] = var * ldexpf(1.0f, -splits_on_axis(d, 2));
+}
+
+__global__ void k_refine_nodes(int64_t n, const NodeW* __restrict__ nodes,
+                               const float* __restrict__ dtau, float tau,
+                               NodeW* __restrict__ out) {
+  const int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (q >= n) return;
+  NodeW nd = nodes[q];
+  if (!(nd.meta & kMetaLeaf) && dtau[q] > tau) nd.B = kRefinedB;
+  out[q] = nd;
+}
+
+}  // namespace trevr2
+
+extern "C" int trevr2_set_tau_refine(trevr2_tree* tree, double tau_refine, void* stream) {
+  clear_error();
+  if (!tree) {
+    set_error("trevr2_set_tau_refine: tree is NULL");
+    return TREVR2_EINVAL;
+  }
+  if (!(tau_refine > 0.0)) {
+    set_error("trevr2_set_tau_refine: tau_refine must be positive (infinity turns it off)");
+    return TREVR2_EINVAL;
+  }
+  Tree* t = reinterpret_cast<Tree*>(tree);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (std::isinf(tau_refine)) {
+    t->refine_on = false;
+    t->tau_refine = tau_refine;
+    return TREVR2_OK;
+  }
+  const int64_t n = t->n_nodes;
+  if (!t->dtau) {
+    T2_CHECK(dalloc(&t->dtau, size_t(n), st));
+    float* range = nullptr;
+    T2_CHECK(dalloc(&range, size_t(n) * 2 * t->nbp, st));
+    float* amin = range;
+    float* amax = range + size_t(n) * t->nbp;
+    for (int d = int(t->level_begin.size()) - 2; d >= 0; --d) {
+      const int64_t lb = t->level_begin[d], le = t->level_begin[d + 1];
+      if (le <= lb) continue;
+      const unsigned g = blocks_for(le - lb, 256);
+      switch (t->nbp) {
+        case 1: k_tau_variation_level<1><<<g, 256, 0, st>>>(lb, le, t->nodes, t->alpha_leaf, amin, amax, t->dtau); break;
+        case 2: k_tau_variation_level<2><<<g, 256, 0, st>>>(lb, le, t->nodes, t->alpha_leaf, amin, amax, t->dtau); break;
+        default: k_tau_variation_level<4><<<g, 256, 0, st>>>(lb, le, t->nodes, t->alpha_leaf, amin, amax, t->dtau); break;
+      }
+      note_launch();
+    }
+    T2_CUDA(cudaGetLastError());
+    dfree(range, st);
+  }
+  if (!t->nodes_refined) T2_CHECK(dalloc(&t->nodes_refined, size_t(n), st));
+  k_refine_nodes<<<blocks_for(n, 256), 256, 0, st>>>(n, t->nodes, t->dtau, float(tau_refine),
+                                                      t->nodes_refined);
+  note_launch();
+  T2_CUDA(cudaGetLastError());
+  t->refine_on = true;
+  t->tau_refine = tau_refine;
   return TREVR2_OK;
 }

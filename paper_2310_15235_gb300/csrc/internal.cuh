@@ -112,6 +112,12 @@ struct Tree {
   double* c64 = nullptr;      // [n][3] normalised centre of luminosity
   double* B64 = nullptr;      // [n] normalised B
   float* alpha_leaf = nullptr;// [n][nbp] normalised bucket absorption (0 internal)
+  // refinement tau_refine (Sec. 2.5.2): node records with B raised where the
+  // optical depth varies by more than tau_refine inside the cell
+  float* dtau = nullptr;          // [n] optical-depth variation of each cell
+  NodeW* nodes_refined = nullptr; // [n], kept until the tree is freed
+  bool refine_on = false;
+  double tau_refine = 0.0;
   std::vector<int64_t> level_begin;  // host: first node of each depth, plus end
 
   std::vector<Table> tables;  // cached per nside

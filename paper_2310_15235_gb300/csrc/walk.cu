@@ -815,7 +815,7 @@ bool valid_nside(int nside) {
 void fill_walk_args(const Tree* t, const Table* tb, int nside, float theta, const int* bsel,
                     int nbsel, uint32_t flags, int M, WalkArgs* a) {
   std::memset(a, 0, sizeof(WalkArgs));
-  a->nodes = t->nodes;
+  a->nodes = t->refine_on ? t->nodes_refined : t->nodes;
   a->csrc = t->csrc;
   a->c64 = t->c64;
   a->B64 = t->B64;

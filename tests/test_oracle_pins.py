@@ -939,3 +939,47 @@ def test_directed_needs_bucket_and_keeps_closed_form(oracle_mod):
     ok = np.all((centres >= 0) & (centres < 1), axis=1)
     np.testing.assert_allclose(J[ok, 0], np.exp(-2.0 * r[ok]) / (4 * np.pi * r[ok] ** 2),
                                rtol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# Refinement tau_refine (Sec. 2.5.2): a cell whose optical depth varies by
+# more than tau_refine inside it opens as well.
+
+def test_tau_variation_brute_force(oracle_mod):
+    """Per cell: (largest - smallest bucket alpha over the leaves under it)
+    times its longest side, the largest over the bands, from the leaves."""
+    case = workloads.random_case(600, 10, nb=2, seed=161, clumped=True)
+    t = oracle_mod.OracleTree.from_case(case)
+    dtau = t.set_tau_refine(0.1)
+    e, ag = t.export(), t.aggregates()
+    leaves = np.flatnonzero(e["child"] < 0)
+    for q in range(len(e["depth"])):
+        lo, hi = e["box"][q, :3], e["box"][q, 3:]
+        inside = [l for l in leaves if np.all(e["box"][l, :3] >= lo) and np.all(e["box"][l, 3:] <= hi)]
+        a = ag["alpha_leaf"][inside]
+        want = (a.max(0) - a.min(0)).max() * (hi - lo).max()
+        assert dtau[q] == pytest.approx(want, rel=1e-12, abs=1e-300)
+
+
+def test_tau_refine_limits(oracle_mod):
+    """A vanishing tau_refine opens every internal cell with any variation
+    inside, i.e. every one that holds gas of random opacity.  With a single
+    luminous gas element (a leaf's centre of luminosity is then that
+    element, so opening leaves changes nothing) this is the theta -> 0 cut;
+    an infinite tau_refine changes nothing."""
+    case = workloads.random_case(400, 0, nb=2, seed=162, clumped=True, n_active=120)
+    case["lum"][17] = np.array([0.8, 0.3], np.float32)
+    t = oracle_mod.OracleTree.from_case(case)
+    act = case["active"]
+    J0 = t.J(act, 2, 0.75)
+    Jfine = t.J(act, 2, 1e-9)
+    for flags in (0, oracle_mod.FLAG_BUCKET):
+        t.set_tau_refine(1e-12)
+        np.testing.assert_allclose(t.J(act, 2, 0.75, flags=flags),
+                                   t.J(act, 2, 1e-9, flags=flags), rtol=1e-12, atol=1e-300)
+    t.set_tau_refine(1e-12)
+    np.testing.assert_allclose(t.J(act, 2, 0.75), Jfine, rtol=1e-12, atol=1e-300)
+    t.set_tau_refine(np.inf)
+    np.testing.assert_array_equal(t.J(act, 2, 0.75), J0)
+    with pytest.raises(ValueError):
+        t.set_tau_refine(0.0)
