@@ -98,20 +98,31 @@ def main():
                    ("linear, per bucket, p-p, thick", BUCKET | PP | THICK | LINEAR)]
         if len(g["sources"]) == 1:  # directed rays aim at the one source
             methods += [("directed, per bucket", BUCKET),
-                        ("directed, per bucket, p-p, thick", BUCKET | PP | THICK)]
+                        ("directed, per bucket, p-p, thick", BUCKET | PP | THICK),
+                        ("refined, per bucket", BUCKET),
+                        ("refined, directed, per bucket", BUCKET)]
+        else:
+            methods += [("linear, refined, per bucket, 192 rays", BUCKET | LINEAR)]
+        # the table's keys for the rows whose name is not their first word
+        keys = {"refined, per bucket": "refined",
+                "refined, directed, per bucket": "refined_directed",
+                "linear, refined, per bucket, 192 rays": "linear_refined_192"}
         for method, flags in methods:
             tg = g["sources"][0] if "directed" in method else None
-            J = tree.J(act_d, case["nside"], case["theta"], flags=flags,
-                       target=tg).cpu().numpy()[:, 0]
+            # absorption refinement with tau_refine = 0.01 (Sec. 3.3, Sec. 3.4)
+            tau = 0.01 if "refined" in method else float("inf")
+            tree.set_tau_refine(tau)
+            ot.set_tau_refine(tau)
+            nside = 4 if "192" in method else case["nside"]
+            J = tree.J(act_d, nside, case["theta"], flags=flags, target=tg).cpu().numpy()[:, 0]
             e, c = esc.figures(J, pts, g)
-            e_o, c_o = esc.figures(ot.J(act, case["nside"], case["theta"], flags=flags,
+            e_o, c_o = esc.figures(ot.J(act, nside, case["theta"], flags=flags,
                                         target=tg)[:, 0], pts, g)
-            t_shell = _time(lambda: tree.J(act_d, case["nside"], case["theta"], flags=flags,
-                                           target=tg))
-            t_all = _time(lambda: tree.J(gas_d, case["nside"], case["theta"], flags=flags,
-                                         target=tg))
+            t_shell = _time(lambda: tree.J(act_d, nside, case["theta"], flags=flags, target=tg))
+            t_all = _time(lambda: tree.J(gas_d, nside, case["theta"], flags=flags, target=tg))
             # the paper's rows come from its per-bucket walk; both are shown
-            paper = table.get((name, method.split(",")[0]), (float("nan"), float("nan")))
+            key = keys.get(method, method.split(",")[0])
+            paper = table.get((name, key), (float("nan"), float("nan")))
             rows.append(dict(test=name, method=method, elements=len(case["pos"]),
                              shell=len(act), escape=e, covering=c, oracle_escape=e_o,
                              oracle_covering=c_o, exact_escape=e_x, exact_covering=c_x,
