@@ -34,6 +34,7 @@ FLAG_THICK = 2
 FLAG_LINEAR = 8
 FLAG_BUCKET = 16
 FLAG_PP = 32
+FLAG_CSM = 64
 
 
 def build(force: bool = False) -> str:
@@ -89,6 +90,8 @@ def _load():
         lib.oracle_beam_tau.argtypes = [P, i64, i32, f64, i64, f64, i32]
         lib.oracle_J_directed.restype = i32
         lib.oracle_J_directed.argtypes = [P, P, i64, i32, f64, u32, P, P, i32]
+        lib.oracle_csm_tables.restype = i32
+        lib.oracle_csm_tables.argtypes = [P, i32, i32, P, P]
         lib.oracle_set_tau_refine.restype = i32
         lib.oracle_set_tau_refine.argtypes = [P, f64, P]
         lib.oracle_pp_sphere.restype = i64
@@ -253,6 +256,15 @@ class OracleTree:
         """Optical depth along beam k of receiver i up to distance s (no r/s)."""
         return _load().oracle_beam_tau(self._h, int(i), int(nside), float(theta), int(k),
                                        float(s), int(band))
+
+    def csm_tables(self, nside, linear=False):
+        """Complex source model (R14): d [nodes][npix] and tau [nodes][npix][nb]."""
+        npix = 12 * nside * nside
+        d = np.empty((self.num_nodes, npix))
+        tau = np.empty((self.num_nodes, npix, self.nb))
+        if _load().oracle_csm_tables(self._h, int(nside), int(bool(linear)), _p(d), _p(tau)) != 0:
+            raise ValueError("bad nside")
+        return d, tau
 
     def set_tau_refine(self, tau_refine):
         """Refinement for every later call (R13; inf turns it off); returns the

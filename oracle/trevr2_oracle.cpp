@@ -73,6 +73,19 @@
 //     also opens.  The variation is read as (largest - smallest bucket alpha
 //     among the leaves under the cell) times the cell's longest side, the
 //     largest over the bands.  Leaves are buckets and never open further.
+//  R14 Complex source model (FLAG_CSM, with FLAG_BUCKET; Sec. 2.7, Eq.
+//     srccomb): every luminous cell keeps, per HEALPix direction k, the
+//     length d_k from its centre of luminosity to its box edge along n_k and
+//     the optical depth tau_k of that ray.  A leaf's is its bucket alpha
+//     times d_k.  A parent's ray ends on the plane through the end of its
+//     own ray, perpendicular to n_k; each luminous child's ray is clipped to
+//     that plane (alpha_child times the shorter length) or extended to it,
+//     the extension absorbing with the sibling's alpha (its direction pair)
+//     over its chord with the sibling's box; L e^{-tau} = sum over children
+//     of L_i e^{-tau_i'} per band.  In the walk, an accepted cell's source
+//     takes the beam's absorption only up to its projected edge s - d_k',
+//     k' the direction from the source back towards the bucket (the pixel of
+//     -n_k), and adds its own tau_k'; single-element sources are as before.
 
 #include <algorithm>
 #include <atomic>
@@ -573,7 +586,78 @@ bool ray_chord(const double x[3], const double n[3], const double blo[3], const 
 }
 
 enum : uint32_t { FLAG_SOFT = 1u, FLAG_THICK = 2u, FLAG_LINEAR = 8u, FLAG_BUCKET = 16u,
-                  FLAG_PP = 32u };
+                  FLAG_PP = 32u, FLAG_CSM = 64u };
+
+// R14: the complex source model's per-cell, per-direction rays.
+struct CsmTables {
+  std::vector<double> d;    // [n][npix] length from the centre of luminosity to the edge
+  std::vector<double> tau;  // [n][npix][nb]
+  std::vector<int64_t> anti;  // [npix] pixel of -n_k
+};
+
+CsmTables csm_tables(const Tree& t, const Aggregates<double>& ag, const std::vector<double>& tab,
+                     int nside) {
+  const int64_t n = static_cast<int64_t>(t.nodes.size());
+  const int nb = t.nb;
+  const int64_t npix = 12 * static_cast<int64_t>(nside) * nside;
+  const int64_t P = npix / 2;
+  std::vector<double> dirs(npix * 3);
+  CsmTables cs;
+  cs.anti.resize(npix);
+  for (int64_t k = 0; k < npix; ++k) pix2vec_ring(nside, k, &dirs[3 * k]);
+  for (int64_t k = 0; k < npix; ++k) {
+    double m[3] = {-dirs[3 * k], -dirs[3 * k + 1], -dirs[3 * k + 2]};
+    cs.anti[k] = vec2pix_ring(nside, m);
+  }
+  cs.d.assign(n * npix, 0.0);
+  cs.tau.assign(n * npix * nb, 0.0);
+  for (int64_t q = n - 1; q >= 0; --q) {
+    if (!(ag.Ltot[q] > 0.0)) continue;
+    const Node& nd = t.nodes[q];
+    double lo[3], hi[3];
+    node_box(nd, t.lo, t.size, lo, hi);
+    const double* c = &ag.c[3 * q];
+    for (int64_t k = 0; k < npix; ++k) {
+      const double* nk = &dirs[3 * k];
+      double t0, t1;
+      const double d = ray_chord(c, nk, lo, hi, t0, t1) ? t1 : 0.0;
+      cs.d[q * npix + k] = d;
+      double* tq = &cs.tau[(q * npix + k) * nb];
+      if (nd.child < 0) {
+        for (int b = 0; b < nb; ++b) tq[b] = ag.alpha[q * nb + b] * d;
+        continue;
+      }
+      std::vector<double> sum(nb, 0.0);
+      for (int64_t i = nd.child; i <= nd.child + 1; ++i) {
+        if (!(ag.Ltot[i] > 0.0)) continue;
+        const int64_t sib = (i == nd.child) ? nd.child + 1 : nd.child;
+        const double* ci = &ag.c[3 * i];
+        // the child's ray to the parent's end plane
+        double D = d;
+        for (int a = 0; a < 3; ++a) D += (c[a] - ci[a]) * nk[a];
+        D = std::max(D, 0.0);
+        const double di = cs.d[i * npix + k];
+        double ext = 0.0;  // the extension's chord with the sibling's box
+        if (D > di) {
+          double slo[3], shi[3], s0, s1;
+          node_box(t.nodes[sib], t.lo, t.size, slo, shi);
+          if (ray_chord(ci, nk, slo, shi, s0, s1))
+            ext = std::max(0.0, std::min(s1, D) - std::max(s0, di));
+        }
+        for (int b = 0; b < nb; ++b) {
+          const double ti = cs.tau[(i * npix + k) * nb + b];
+          double tc;
+          if (D <= di) tc = di > 0.0 ? ti * (D / di) : 0.0;
+          else tc = ti + tab[(sib * P + pair_of_pixel(nside, k)) * nb + b] * ext;
+          sum[b] += ag.L[i * nb + b] * std::exp(-tc);
+        }
+      }
+      for (int b = 0; b < nb; ++b)
+        tq[b] = ag.L[q * nb + b] > 0.0 ? -std::log(sum[b] / ag.L[q * nb + b]) : 0.0;
+    }
+  }
+  return cs;
+}
 
 struct WalkStats {
   int64_t visited = 0;   // nodes given the opening test
@@ -601,6 +685,7 @@ struct Problem {
   double target[3] = {0, 0, 0};
   double tau_refine = std::numeric_limits<double>::infinity();  // R13
   const std::vector<double>* dtau = nullptr;                     // [nodes]
+  const CsmTables* csm = nullptr;                                // R14
   std::vector<double> pp_r;                  // [nodes] r_pp of each leaf (FLAG_PP)
   std::vector<std::vector<int64_t>> pp_list; // [nodes] its p-p particles (original)
 };
@@ -681,6 +766,7 @@ void walk_receiver(const Problem<T>& pr, int64_t i_orig, T* Jout, WalkStats* st)
     T p[3];
     const T* L;         // nb luminosities
     int64_t elem = -1;  // the element, for a single-element source
+    int64_t node = -1;  // the cell, for an accepted cell's source
   };
   std::vector<CutCell> cut;
   std::vector<Src> srcs;
@@ -710,6 +796,7 @@ void walk_receiver(const Problem<T>& pr, int64_t i_orig, T* Jout, WalkStats* st)
         Src s;
         for (int a = 0; a < 3; ++a) s.p[a] = ag.c[3 * q + a];
         s.L = &ag.L[q * nb];
+        s.node = q;
         srcs.push_back(s);
       }
     } else if (nd.child < 0) {
@@ -794,13 +881,24 @@ void walk_receiver(const Problem<T>& pr, int64_t i_orig, T* Jout, WalkStats* st)
         for (int b = 0; b < nb; ++b) taupp[b] += (*pr.kappa)[j * nb + b] * sigma;
       }
     }
+    // R14: a cell source's own ray replaces the beam beyond its projected edge
+    T s_abs = sp;
+    const double* tcsm = nullptr;
+    if (pr.csm && s.node >= 0) {
+      const int64_t ka = pr.csm->anti[k];
+      const int64_t npx = static_cast<int64_t>(pr.dirs.size() / 3);
+      s_abs = sp - pr.csm->d[s.node * npx + ka];
+      if (val(s_abs) < 0.0) s_abs = T(0.0);
+      tcsm = &pr.csm->tau[(s.node * npx + ka) * nb];
+    }
     for (int b = 0; b < nb; ++b) {
       T tau = 0.0;
       for (const Seg& sg : segs[k]) {
-        if (val(sp) <= sg.t0) continue;
-        T len = (val(sp) < sg.t1) ? (sp - sg.t0) : T(sg.t1 - sg.t0);
+        if (val(s_abs) <= sg.t0) continue;
+        T len = (val(s_abs) < sg.t1) ? (s_abs - sg.t0) : T(sg.t1 - sg.t0);
         tau += sg.alpha[b] * len;
       }
+      if (tcsm) tau += tcsm[b];
       tau = tau * (r / sp) + taupp[b];
       Jout[b] += s.L[b] * exp(-tau) * g;
     }
@@ -909,7 +1007,13 @@ struct OracleTree {
   bool tab_linear = false;
   double tau_refine = std::numeric_limits<double>::infinity();  // R13
   std::vector<double> dtau;                                      // [nodes]
+  CsmTables csm;                                                 // R14
+  int csm_nside = -1;
+  bool csm_linear = false;
 };
+
+// R14: the complex source model for this nside and averaging, on first use.
+void ensure_csm(OracleTree& ot, int nside, bool linear);
 
 // R13: the optical-depth variation inside every cell, from the leaves up
 // (children come after their parent in breadth-first order).
@@ -952,6 +1056,15 @@ void ensure_table(OracleTree& ot, int nside, bool linear = false) {
   ot.tab_nside = nside;
   ot.tab_linear = linear;
 }
+
+void ensure_csm(OracleTree& ot, int nside, bool linear) {
+  ensure_table(ot, nside, linear);
+  if (ot.csm_nside == nside && ot.csm_linear == linear) return;
+  ot.csm = csm_tables(ot.t, ot.ag, ot.tab, nside);
+  ot.csm_nside = nside;
+  ot.csm_linear = linear;
+}
+
 
 bool valid_nside(int nside) { return nside >= 1 && nside <= 64 && (nside & (nside - 1)) == 0; }
 
@@ -1101,14 +1214,16 @@ double oracle_thick_factor(double tau) { return thick_factor<double>(tau); }
 int oracle_J(void* h, const int64_t* active, int64_t A, int nside, double theta, uint32_t flags,
              double* J, int nthreads, int64_t* stats) {
   if (!valid_nside(nside) || !(theta > 0.0)) return -1;
-  if ((flags & FLAG_PP) && !(flags & FLAG_BUCKET)) return -1;
+  if ((flags & (FLAG_PP | FLAG_CSM)) && !(flags & FLAG_BUCKET)) return -1;
   OracleTree& ot = *static_cast<OracleTree*>(h);
   for (int64_t a = 0; a < A; ++a)
     if (active[a] < 0 || active[a] >= ot.t.N) return -1;
   ensure_table(ot, nside, (flags & FLAG_LINEAR) != 0);
+  if (flags & FLAG_CSM) ensure_csm(ot, nside, (flags & FLAG_LINEAR) != 0);
   Problem<double> pr = make_problem<double>(ot.t, ot.ag, ot.tab, ot.t.kappa, ot.t.lum, nside,
                                             theta, flags);
   apply_refine(ot, pr);
+  if (flags & FLAG_CSM) pr.csm = &ot.csm;
   prepare_pp(pr, active, A, nthreads);
   const int nb = ot.t.nb;
   parallel_for(A, nthreads, [&](int64_t a) {
@@ -1133,9 +1248,11 @@ int oracle_J_directed(void* h, const int64_t* active, int64_t A, int nside, doub
   for (int64_t a = 0; a < A; ++a)
     if (active[a] < 0 || active[a] >= ot.t.N) return -1;
   ensure_table(ot, nside, (flags & FLAG_LINEAR) != 0);
+  if (flags & FLAG_CSM) ensure_csm(ot, nside, (flags & FLAG_LINEAR) != 0);
   Problem<double> pr = make_problem<double>(ot.t, ot.ag, ot.tab, ot.t.kappa, ot.t.lum, nside,
                                             theta, flags);
   apply_refine(ot, pr);
+  if (flags & FLAG_CSM) pr.csm = &ot.csm;
   pr.directed = true;
   for (int a = 0; a < 3; ++a) pr.target[a] = target[a];
   prepare_pp(pr, active, A, nthreads);
@@ -1151,7 +1268,7 @@ int oracle_J_directed(void* h, const int64_t* active, int64_t A, int nside, doub
 // beams and the tree stay those of the primal inputs.
 int oracle_J_deriv(void* h, const int64_t* active, int64_t A, int nside, double theta,
                    uint32_t flags, int which, int64_t elem, int band, double* dJ, int nthreads) {
-  if (!valid_nside(nside) || !(theta > 0.0)) return -1;
+  if (!valid_nside(nside) || !(theta > 0.0) || (flags & FLAG_CSM)) return -1;
   if ((flags & FLAG_PP) && !(flags & FLAG_BUCKET)) return -1;
   OracleTree& ot = *static_cast<OracleTree*>(h);
   const Tree& t = ot.t;
@@ -1190,6 +1307,17 @@ int64_t oracle_pp_sphere(void* h, int64_t i, int nside, double* rpp, int64_t* li
   std::sort(l.begin(), l.end());
   if (list) std::copy(l.begin(), l.end(), list);
   return static_cast<int64_t>(l.size());
+}
+
+// R14: the complex source model's d [n][npix] and tau [n][npix][nb] for
+// this nside and averaging (linear != 0).  Returns 0 or -1.
+int oracle_csm_tables(void* h, int nside, int linear, double* d, double* tau) {
+  OracleTree& ot = *static_cast<OracleTree*>(h);
+  if (!valid_nside(nside)) return -1;
+  ensure_csm(ot, nside, linear != 0);
+  std::copy(ot.csm.d.begin(), ot.csm.d.end(), d);
+  std::copy(ot.csm.tau.begin(), ot.csm.tau.end(), tau);
+  return 0;
 }
 
 // R13: refinement for every later call; tau_refine <= 0 or NaN is

@@ -983,3 +983,102 @@ def test_tau_refine_limits(oracle_mod):
     np.testing.assert_array_equal(t.J(act, 2, 0.75), J0)
     with pytest.raises(ValueError):
         t.set_tau_refine(0.0)
+
+
+# ----------------------------------------------------------------------------
+# Complex source model (Sec. 2.7, Eq. srccomb; flags BUCKET | CSM)
+
+def _exit_by_marching(c, n, lo, hi):
+    """Distance from c along n to the first point outside [lo, hi), by
+    bisection on the inside test."""
+    a, b = 0.0, 4.0 * np.linalg.norm(hi - lo)
+    for _ in range(80):
+        m = 0.5 * (a + b)
+        p = c + m * n
+        if np.all(p >= lo) and np.all(p < hi):
+            a = m
+        else:
+            b = m
+    return a
+
+
+def test_csm_leaf_rays(oracle_mod):
+    """A luminous leaf's ray in direction k runs from its centre of
+    luminosity to its box edge; its optical depth is the bucket alpha times
+    that length."""
+    case = workloads.random_case(300, 12, nb=2, seed=181, clumped=True)
+    t = oracle_mod.OracleTree.from_case(case)
+    e, ag = t.export(), t.aggregates()
+    d, tau = t.csm_tables(1)
+    dirs = oracle_mod.pix2vec(1)
+    lit = np.flatnonzero((e["child"] < 0) & (ag["Ltot"] > 0))
+    assert len(lit) > 3
+    for q in lit:
+        lo, hi = e["box"][q, :3], e["box"][q, 3:]
+        for k in range(12):
+            want = _exit_by_marching(ag["c"][q], dirs[k], lo, hi)
+            assert d[q, k] == pytest.approx(want, abs=1e-12)
+            np.testing.assert_allclose(tau[q, k], ag["alpha_leaf"][q] * d[q, k], rtol=1e-13)
+
+
+def test_csm_single_star_is_the_line_integral(oracle_mod):
+    """One star under a root whose halves are leaves: the root's centre of
+    luminosity is the star, so its ray in every direction is the line
+    integral of the two buckets' alpha from the star to the root's edge
+    (the star's own leaf, then the extension through the sibling)."""
+    rng = np.random.default_rng(182)
+    gas = rng.uniform(0, 1, (14, 3))
+    star = np.array([[0.3, 0.62, 0.45]])
+    pos = np.concatenate([gas, star])
+    n = len(pos)
+    mass = np.concatenate([rng.uniform(0.5, 1.5, 14) / 14, [0.0]])
+    kappa = np.concatenate([rng.uniform(1.0, 30.0, (14, 2)), [[0.0, 0.0]]])
+    lum = np.zeros((n, 2))
+    lum[-1] = [1.0, 0.4]
+    case = workloads._pack("two_leaves", pos, mass, kappa, lum, np.full(n, 0.2),
+                           np.arange(14), 2, 0.75, bucket=12)
+    t = oracle_mod.OracleTree.from_case(case)
+    e, ag = t.export(), t.aggregates()
+    assert e["child"][0] == 1 and np.all(e["child"][1:3] < 0)  # root and two leaves
+    for nside in (1, 2):
+        d, tau = t.csm_tables(nside)
+        dirs = oracle_mod.pix2vec(nside)
+        for k in range(len(dirs)):
+            L = _exit_by_marching(star[0], dirs[k], e["box"][0, :3], e["box"][0, 3:])
+            assert d[0, k] == pytest.approx(L, abs=1e-12)
+            m = 20000
+            ts = (np.arange(m) + 0.5) / m * L
+            pts = star[0][None, :] + ts[:, None] * dirs[k][None, :]
+            ax = e["depth"][0] % 3
+            mid = 0.5 * (e["box"][0, ax] + e["box"][0, 3 + ax])
+            leaf = 1 + (pts[:, ax] >= mid)
+            want = ag["alpha_leaf"][leaf].sum(0) * (L / m)
+            np.testing.assert_allclose(tau[0, k], want, rtol=2e-4, atol=1e-12)
+
+
+@pytest.mark.parametrize("nside,theta", [(2, 0.75), (1, 0.3), (4, 1.5)])
+def test_csm_closed_form_one_source(oracle_mod, nside, theta):
+    """One source in a uniform medium: every cell holding it has the source
+    as its centre of luminosity, so its rays are kappa rho times their
+    length, and the beam cut at s - d plus the cell's own ray gives kappa
+    rho s: J = L e^{-kappa rho r} / (4 pi r^2) at every receiver whose
+    bucket beam stays in the box."""
+    case = workloads.uniform_point_source(offset=True)
+    t = oracle_mod.OracleTree.from_case(case)
+    J = t.J(case["active"], nside, theta, flags=oracle_mod.FLAG_BUCKET | oracle_mod.FLAG_CSM)
+    J0 = t.J(case["active"], nside, theta, flags=oracle_mod.FLAG_BUCKET)
+    src = case["pos"][-1]
+    centres = _leaf_centres(t, len(case["pos"]))
+    dirs = oracle_mod.pix2vec(nside)
+    ok = np.ones(len(case["active"]), dtype=bool)
+    for a, i in enumerate(case["active"]):
+        v = src - centres[i]
+        k = oracle_mod.vec2pix(nside, v[None])[0]
+        q = centres[i] + (v @ dirs[k]) * dirs[k]
+        ok[a] = np.all(q >= 0) and np.all(q < 1)
+    r = np.linalg.norm(case["pos"][case["active"]] - src, axis=1)
+    np.testing.assert_allclose(J[ok, 0], np.exp(-2.0 * r[ok]) / (4 * np.pi * r[ok] ** 2),
+                               rtol=1e-12)
+    np.testing.assert_allclose(J[ok], J0[ok], rtol=1e-12)
+    with pytest.raises(ValueError):
+        t.J(case["active"][:3], nside, theta, flags=oracle_mod.FLAG_CSM)
