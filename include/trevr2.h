@@ -58,6 +58,8 @@ extern "C" {
                              distance over the projected one (trevr2_J only) */
 #define TREVR2_PP 32u    /* with TREVR2_BUCKET: particle-particle absorption inside
                             the bucket's p-p radius (Sec. 2.4; trevr2_J only) */
+#define TREVR2_CSM 64u   /* with TREVR2_BUCKET: the complex source model (Sec. 2.7,
+                            Eq. srccomb; trevr2_J and trevr2_J_directed only) */
 
 /* Supported sizes: 1 <= nb <= 4 bands; nside a power of two in [1, 16];
  * N < 2^31 elements; 1 <= bucket <= 4096. */
@@ -108,7 +110,7 @@ int trevr2_build(const double* pos, const float* mass, const float* kappa, const
  *  theta   opening parameter theta_rad > 0 (paper default 0.75)
  *  bands   host [nbsel] band indices to return, or NULL = all nb bands
  *  flags   TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_BUCKET |
- *          TREVR2_PP | TREVR2_ASYNC.  With TREVR2_BUCKET the cut, the beam of each source,
+ *          TREVR2_PP | TREVR2_CSM | TREVR2_ASYNC.  With TREVR2_BUCKET the cut, the beam of each source,
  *          its projected distance s and the optical depth to s are those of
  *          the centre of the leaf box holding the receiver, shared by every
  *          receiver of that leaf; each receiver adds L g(r) e^{-tau r/s} with
@@ -123,8 +125,17 @@ int trevr2_build(const double* pos, const float* mass, const float* kappa, const
  *          (not the receiver, not the source) closer to the source than the
  *          receiver and within h_k of the segment (distance b) adds
  *          kappa_k 3 m_k (1 - b / h_k) / (pi h_k^2).  A sphere holding more
- *          than 4096 particles gives EUNSUPPORTED.  trevr2_J_backward, the
- *          batches and trevr2_J_noalloc take neither flag (EUNSUPPORTED,
+ *          than 4096 particles gives EUNSUPPORTED.  TREVR2_CSM (needs
+ *          TREVR2_BUCKET, else EINVAL) adds Sec. 2.7: every luminous cell
+ *          keeps, per HEALPix direction, the ray from its centre of
+ *          luminosity to its box edge (leaves: bucket alpha times length;
+ *          parents: the children's rays clipped or extended, through the
+ *          sibling, to the parent's end plane and combined by Eq. srccomb),
+ *          built per nside and averaging on first use ([nodes][N_ray] per
+ *          band and length); an accepted cell's source then takes the beam
+ *          only up to its projected edge s - d and adds its own ray towards
+ *          the bucket.  trevr2_J_backward, the batches and trevr2_J_noalloc
+ *          take none of TREVR2_BUCKET, TREVR2_PP, TREVR2_CSM (EUNSUPPORTED,
  *          EUNSUPPORTED, EINVAL).
  *  J       [A][nbsel] float32 output, overwritten
  * Active indices outside [0, N) give EINVAL (their rows are set to NaN).

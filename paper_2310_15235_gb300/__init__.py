@@ -25,7 +25,7 @@ import torch
 __all__ = [
     "SOFT", "THICK", "ASYNC", "Tree", "TrevrError", "build", "J", "library_path", "load_library",
     "healpix_pix2vec", "healpix_vec2pix", "exported_symbols", "FIELDS", "kernel_launches",
-    "Batch", "J_batched", "J_fn", "LINEAR", "BUCKET", "PP",
+    "Batch", "J_batched", "J_fn", "LINEAR", "BUCKET", "PP", "CSM",
 ]
 
 SOFT = 1
@@ -34,6 +34,7 @@ ASYNC = 4
 LINEAR = 8  # linear absorption averaging (Sec. 2.6's comparison scheme)
 BUCKET = 16  # per-bucket beams from the bucket centre (Sec. 2.5.1), trevr2_J only
 PP = 32  # with BUCKET: particle-particle absorption inside r_pp (Sec. 2.4)
+CSM = 64  # with BUCKET: the complex source model (Sec. 2.7)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libtrevr2.so")

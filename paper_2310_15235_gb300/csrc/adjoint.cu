@@ -656,8 +656,9 @@ extern "C" int trevr2_J_backward(trevr2_tree* tree, const int64_t* active, int64
     set_error("trevr2_J_backward: theta must be positive and finite");
     return TREVR2_EINVAL;
   }
-  if (flags & (TREVR2_BUCKET | TREVR2_PP)) {
-    set_error("trevr2_J_backward: TREVR2_BUCKET and TREVR2_PP are trevr2_J flags only");
+  if (flags & (TREVR2_BUCKET | TREVR2_PP | TREVR2_CSM)) {
+    set_error("trevr2_J_backward: TREVR2_BUCKET, TREVR2_PP and TREVR2_CSM are trevr2_J flags "
+              "only");
     return TREVR2_EUNSUPPORTED;
   }
   if (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_ASYNC)) {

@@ -573,6 +573,9 @@ static void free_tree(Tree* t, cudaStream_t st) {
     dfree(tb.dirs, st);
     dfree(tb.dirs64, st);
     dfree(tb.geo, st);
+    dfree(tb.csm_tau, st);
+    dfree(tb.csm_d, st);
+    dfree(tb.csm_anti, st);
   }
   t->tables.clear();
   if (t->scratch) cudaFreeAsync(t->scratch, st);

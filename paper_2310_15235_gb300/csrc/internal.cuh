@@ -71,6 +71,10 @@ struct Table {
   float4* dirs = nullptr;      // [npix] beam directions (xyz), w = pair index (int bits)
   double* dirs64 = nullptr;    // [npix][3]
   TransGeo* geo = nullptr;     // [3][P]
+  // complex source model (Sec. 2.7), built on first use with TREVR2_CSM
+  float* csm_tau = nullptr;    // [n][npix][nbp] optical depth of each luminous cell's ray
+  float* csm_d = nullptr;      // [n][npix] its length (normalised)
+  int* csm_anti = nullptr;     // [npix] pixel of -n_k
 };
 
 // ---------------------------------------------------------------------------

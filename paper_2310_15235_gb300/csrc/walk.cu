@@ -36,6 +36,17 @@
 
 namespace trevr2 {
 
+// Complex source model (Sec. 2.7): a cell's source adds its own ray's optical
+// depth towards the bucket (direction -n_k) to the beam's.
+template <int NBP>
+__device__ __forceinline__ void add_csm(const WalkArgs& a, int ref, int k, BandVec<NBP>& tk) {
+  if (!a.csm_tau || (ref & kRefElement)) return;
+  const BandVec<NBP> c =
+      load_bands<NBP>(a.csm_tau + (int64_t(ref) * a.npix + a.csm_anti[k]) * NBP);
+#pragma unroll
+  for (int b = 0; b < NBP; ++b) tk.v[b] += c.v[b];
+}
+
 // Phase A: lanes take beams from the order above through a per-warp counter.
 // Each beam first descends the receiver's ancestors (chain[0..], root to the
 // receiver's leaf, in shared memory): they hold the receiver, so they open,
@@ -83,6 +94,7 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
         BandVec<NBP> tk;
 #pragma unroll
         for (int b = 0; b < NBP; ++b) tk.v[b] = tau[b] + al.v[b] * ds;
+        if constexpr (kBucket) add_csm<NBP>(a, V[ptr].ref, k, tk);
         store_bands<NBP>(T + int64_t(ptr) * NBP, tk);
         ++ptr;
         s_next = ptr < end ? V[ptr].s : INFINITY;
@@ -136,7 +148,15 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
     BandVec<NBP> tk;
 #pragma unroll
     for (int b = 0; b < NBP; ++b) tk.v[b] = tau[b];
-    for (; ptr < end; ++ptr) store_bands<NBP>(T + int64_t(ptr) * NBP, tk);
+    for (; ptr < end; ++ptr) {
+      if constexpr (kBucket) {
+        BandVec<NBP> tc = tk;
+        add_csm<NBP>(a, V[ptr].ref, k, tc);
+        store_bands<NBP>(T + int64_t(ptr) * NBP, tc);
+      } else {
+        store_bands<NBP>(T + int64_t(ptr) * NBP, tk);
+      }
+    }
     idx = atomicAdd(next_beam, 1);
   }
 }
@@ -517,7 +537,7 @@ __device__ __forceinline__ void eval_bucket(const WalkArgs& a, bool soft, int la
         pp_tau<NBP>(a, npp, ppw, ppxh, ppkc, ppsi, si, p,
                     elem ? a.pos64 + 3 * id : a.c64 + 3 * id, elem ? int(id) : -1, vx, vy, vz,
                     r, tpp);
-      const float rs = r / src.s;
+      const float rs = r / src.w;  // w: the source's projected distance
       const BandVec<NBP> L = load_bands<NBP>(elem ? a.Lelem + id * NBP : a.Lnode + id * NBP);
       const BandVec<NBP> tk = load_bands<NBP>(T + int64_t(e) * NBP);
 #pragma unroll
@@ -961,6 +981,140 @@ static int launch_walk(Tree* t, Table* tb, const int64_t* active, int64_t A, int
   return TREVR2_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Complex source model tables (Sec. 2.7, Eq. srccomb), one depth at a time,
+// deepest first, a thread per (cell, direction k).  A luminous cell's ray
+// runs from its centre of luminosity along n_k to its box edge (length d);
+// a leaf's optical depth is its bucket alpha times d.  A parent's ray ends
+// on the plane through the end of its own ray, perpendicular to n_k: each
+// luminous child's ray is clipped to that plane or extended to it through
+// the sibling (the sibling's alpha for this direction pair over the
+// extension's chord with its box), and L e^{-tau} = sum_i L_i e^{-tau_i'}
+// per band, evaluated with the smallest tau_i' factored out so that opaque
+// children do not underflow.
+__global__ void k_csm_anti(int nside, int npix, const double* __restrict__ dirs64,
+                           int* __restrict__ anti) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= npix) return;
+  anti[k] = hp_vec2pix_f64(nside, -dirs64[3 * k], -dirs64[3 * k + 1], -dirs64[3 * k + 2]);
+}
+
+template <int NBP>
+__global__ void k_csm_level(int64_t lb, int64_t le, int npix, int P,
+                            const NodeW* __restrict__ nodes, const float4* __restrict__ csrc,
+                            const float* __restrict__ Lnode, const float* __restrict__ alpha_leaf,
+                            const float* __restrict__ alpha_tab, const float4* __restrict__ dirs,
+                            float* __restrict__ csm_d, float* __restrict__ csm_tau) {
+  const int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (idx >= (le - lb) * npix) return;
+  const int64_t q = lb + idx / npix;
+  const int k = int(idx % npix);
+  const NodeW nd = nodes[q];
+  if (!(nd.meta & kMetaHasL)) return;  // left at zero
+  const float4 dn = dirs[k];
+  const int pair = __float_as_int(dn.w);
+  const float n[3] = {dn.x, dn.y, dn.z};
+  float inv[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) inv[c] = n[c] != 0.0f ? 1.0f / n[c] : 0.0f;
+  const float4 cq = csrc[q];
+  const float xq[3] = {cq.x, cq.y, cq.z};
+  float t0, t1;
+  const float d = beam_chord(nd, xq, n, inv, INFINITY, t0, t1) ? t1 : 0.0f;
+  csm_d[q * npix + k] = d;
+  float* out = csm_tau + (q * npix + k) * NBP;
+  if (nd.meta & kMetaLeaf) {
+#pragma unroll
+    for (int b = 0; b < NBP; ++b) out[b] = alpha_leaf[q * NBP + b] * d;
+    return;
+  }
+  float tc[2][NBP], Lc[2][NBP];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t i = nd.child + h;
+    const NodeW ni = nodes[i];
+#pragma unroll
+    for (int b = 0; b < NBP; ++b) {
+      tc[h][b] = 0.0f;
+      Lc[h][b] = 0.0f;
+    }
+    if (!(ni.meta & kMetaHasL)) continue;
+    const float4 ci = csrc[i];
+    const float xi[3] = {ci.x, ci.y, ci.z};
+    const float D = fmaxf((cq.x - ci.x) * n[0] + (cq.y - ci.y) * n[1] + (cq.z - ci.z) * n[2] + d,
+                          0.0f);
+    const float di = csm_d[i * npix + k];
+    const int64_t sib = nd.child + (1 - h);
+    const NodeW ns = nodes[sib];
+    float ext = 0.0f;
+    if (D > di) {
+      float s0, s1;
+      if (beam_chord(ns, xi, n, inv, INFINITY, s0, s1))
+        ext = fmaxf(0.0f, fminf(s1, D) - fmaxf(s0, di));
+    }
+#pragma unroll
+    for (int b = 0; b < NBP; ++b) {
+      const float ti = csm_tau[(i * npix + k) * NBP + b];
+      const float as = (ns.meta & kMetaLeaf) ? alpha_leaf[sib * NBP + b]
+                                             : alpha_tab[(int64_t(ns.aux) * P + pair) * NBP + b];
+      tc[h][b] = D <= di ? (di > 0.0f ? ti * (D / di) : 0.0f) : ti + as * ext;
+      Lc[h][b] = Lnode[i * NBP + b];
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < NBP; ++b) {
+    const float Lq = Lnode[q * NBP + b];
+    float m = INFINITY;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      if (Lc[h][b] > 0.0f) m = fminf(m, tc[h][b]);
+    if (!(Lq > 0.0f) || !(m < INFINITY)) {
+      out[b] = 0.0f;
+      continue;
+    }
+    float S = 0.0f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      if (Lc[h][b] > 0.0f) S += Lc[h][b] * expf(-(tc[h][b] - m));
+    out[b] = m - logf(S / Lq);
+  }
+}
+
+// The complex source model tables for this table's nside and averaging.
+static int ensure_csm(Tree* t, Table* tb, cudaStream_t st) {
+  if (tb->csm_tau) return TREVR2_OK;
+  const int npix = 12 * tb->nside * tb->nside, P = npix / 2;
+  const int64_t n = t->n_nodes;
+  const size_t ntau = size_t(n) * npix * t->nbp, nd = size_t(n) * npix;
+  for (float** p : {&tb->csm_tau, &tb->csm_d}) {
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(p),
+                                    (p == &tb->csm_tau ? ntau : nd) * sizeof(float), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(complex source model)");
+  }
+  {
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tb->csm_anti), npix * sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(complex source model)");
+  }
+  T2_CUDA(cudaMemsetAsync(tb->csm_tau, 0, ntau * sizeof(float), st));
+  T2_CUDA(cudaMemsetAsync(tb->csm_d, 0, nd * sizeof(float), st));
+  k_csm_anti<<<(npix + 127) / 128, 128, 0, st>>>(tb->nside, npix, tb->dirs64, tb->csm_anti);
+  note_launch();
+  for (int d = t->max_depth; d >= 0; --d) {
+    const int64_t lb = t->level_begin[d], le = t->level_begin[d + 1];
+    const int64_t work = (le - lb) * npix;
+    if (work <= 0) continue;
+    const unsigned blocks = unsigned((work + 255) / 256);
+    switch (t->nbp) {
+      case 1: k_csm_level<1><<<blocks, 256, 0, st>>>(lb, le, npix, P, t->nodes, t->csrc, t->Lnode, t->alpha_leaf, tb->alpha, tb->dirs, tb->csm_d, tb->csm_tau); break;
+      case 2: k_csm_level<2><<<blocks, 256, 0, st>>>(lb, le, npix, P, t->nodes, t->csrc, t->Lnode, t->alpha_leaf, tb->alpha, tb->dirs, tb->csm_d, tb->csm_tau); break;
+      default: k_csm_level<4><<<blocks, 256, 0, st>>>(lb, le, npix, P, t->nodes, t->csrc, t->Lnode, t->alpha_leaf, tb->alpha, tb->dirs, tb->csm_d, tb->csm_tau); break;
+    }
+    note_launch();
+  }
+  T2_CUDA(cudaGetLastError());
+  return TREVR2_OK;
+}
+
 template <int NBP>
 static const void* bucket_kernel_nbp(bool pp) {
   return pp ? reinterpret_cast<const void*>(&k_walk_bucket<NBP, kWalkWarps, true>)
@@ -1006,6 +1160,12 @@ static int launch_walk_bucket(Tree* t, Table* tb, const int64_t* active, int64_t
   k_bucket_leaf<<<gb, 256, 0, st>>>(t->child, t->first, keys, A, t->N, leaf);
   note_launch();
   a.order = slots;
+  if (flags & TREVR2_CSM) {
+    T2_CHECK(ensure_csm(t, tb, st));
+    a.csm_tau = tb->csm_tau;
+    a.csm_d = tb->csm_d;
+    a.csm_anti = tb->csm_anti;
+  }
   BucketArgs bk;
   std::memset(&bk, 0, sizeof(bk));
   bk.keys = keys;
@@ -1118,12 +1278,12 @@ static int J_impl(trevr2_tree* tree, const int64_t* active, int64_t A, int nside
     return TREVR2_EINVAL;
   }
   if (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_ASYNC | TREVR2_BUCKET |
-                TREVR2_PP)) {
+                TREVR2_PP | TREVR2_CSM)) {
     set_error("trevr2_J: unknown flag bits 0x%x", flags);
     return TREVR2_EINVAL;
   }
-  if ((flags & TREVR2_PP) && !(flags & TREVR2_BUCKET)) {
-    set_error("trevr2_J: TREVR2_PP needs TREVR2_BUCKET");
+  if ((flags & (TREVR2_PP | TREVR2_CSM)) && !(flags & TREVR2_BUCKET)) {
+    set_error("trevr2_J: TREVR2_PP and TREVR2_CSM need TREVR2_BUCKET");
     return TREVR2_EINVAL;
   }
   int bsel[TREVR2_MAX_BANDS];
@@ -1292,8 +1452,9 @@ extern "C" int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const 
               TREVR2_MAX_NSIDE);
     return nside > TREVR2_MAX_NSIDE ? TREVR2_EUNSUPPORTED : TREVR2_EINVAL;
   }
-  if (flags & (TREVR2_BUCKET | TREVR2_PP)) {
-    set_error("trevr2_batch_create: TREVR2_BUCKET and TREVR2_PP are trevr2_J flags only");
+  if (flags & (TREVR2_BUCKET | TREVR2_PP | TREVR2_CSM)) {
+    set_error("trevr2_batch_create: TREVR2_BUCKET, TREVR2_PP and TREVR2_CSM are trevr2_J "
+              "flags only");
     return TREVR2_EUNSUPPORTED;
   }
   if (!(theta > 0.0f) || !std::isfinite(theta) || (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_ASYNC))) {

@@ -60,6 +60,10 @@ struct WalkArgs {
   int max_depth;
   uint32_t* status;
   unsigned long long* counter;
+  // complex source model (per-bucket walk with TREVR2_CSM; NULL when off)
+  const float* csm_tau;  // [n][npix][nbp]
+  const float* csm_d;    // [n][npix]
+  const int* csm_anti;   // [npix]
 };
 
 __device__ __forceinline__ float3 node_ext(uint32_t meta) {
@@ -306,8 +310,18 @@ __device__ __forceinline__ bool make_source(const WalkArgs& a, float3 p, const d
   if (!(s > 0.0f)) return false;
   out.s = s;
   out.rs = r / s;
-  if constexpr (kBucket) out.w = 0.0f;
-  else out.w = (a.flags & TREVR2_SOFT) ? soft_kernel(r, a.hn[si]) : 1.0f / (kFourPi * r2);
+  if constexpr (kBucket) {
+    // the bucket walk keeps the projected distance in w; with the complex
+    // source model (Sec. 2.7) a cell's source takes the beam only up to its
+    // projected edge s - d, d its own ray back towards the bucket
+    out.w = s;
+    if (a.csm_tau && !(ref & kRefElement)) {
+      const float d = a.csm_d[int64_t(ref) * a.npix + a.csm_anti[k]];
+      out.s = fmaxf(s - d, 1e-30f);
+    }
+  } else {
+    out.w = (a.flags & TREVR2_SOFT) ? soft_kernel(r, a.hn[si]) : 1.0f / (kFourPi * r2);
+  }
   out.ref = ref;
   pix = k;
   return true;

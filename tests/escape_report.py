@@ -32,6 +32,7 @@ LINEAR = 8
 BUCKET = 16
 PP = 32
 THICK = 2
+CSM = 64
 NAMES = ["two_sources_cloud", "source_two_clouds", "source_wall"]
 
 
@@ -103,10 +104,12 @@ def main():
                         ("refined, directed, per bucket", BUCKET)]
         else:
             methods += [("linear, refined, per bucket, 192 rays", BUCKET | LINEAR)]
+        methods += [("complex source, per bucket", BUCKET | CSM)]
         # the table's keys for the rows whose name is not their first word
         keys = {"refined, per bucket": "refined",
                 "refined, directed, per bucket": "refined_directed",
-                "linear, refined, per bucket, 192 rays": "linear_refined_192"}
+                "linear, refined, per bucket, 192 rays": "linear_refined_192",
+                "complex source, per bucket": "complex"}
         for method, flags in methods:
             tg = g["sources"][0] if "directed" in method else None
             # absorption refinement with tau_refine = 0.01 (Sec. 3.3, Sec. 3.4)
