@@ -336,6 +336,16 @@ def run_ours(args, world, rank, local):
             extra["bucket_pp"]["parity_sample"] = {"receivers": 128,
                                                    "median_rel": float(np.median(rel)),
                                                    "max_rel": float(rel.max())}
+            # the complex source model (tables built in the warm-up call)
+            extra["bucket_csm"] = run_bucket(case, inp, dev, walk_avg, reps=2,
+                                             extra_flags=t2.CSM, kernel="k_walk_bucket (CSM)")
+            ref = ot.J(sample[:128], case["nside"], case["theta"], flags=t2.BUCKET | t2.CSM,
+                       nthreads=cores)
+            got = extra["bucket_csm"].pop("_J")[sample[:128]]
+            rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
+            extra["bucket_csm"]["parity_sample"] = {"receivers": 128,
+                                                    "median_rel": float(np.median(rel)),
+                                                    "max_rel": float(rel.max())}
     elif world == 1 and not args.no_bucket:
         extra["bucket"] = run_bucket(case, inp, dev, walk_avg)
         extra["bucket"].pop("_J")
@@ -343,6 +353,9 @@ def run_ours(args, world, rank, local):
                                         extra_flags=t2.PP | t2.THICK,
                                         kernel="k_walk_bucket (p-p)")
         extra["bucket_pp"].pop("_J")
+        extra["bucket_csm"] = run_bucket(case, inp, dev, walk_avg, reps=2,
+                                         extra_flags=t2.CSM, kernel="k_walk_bucket (CSM)")
+        extra["bucket_csm"].pop("_J")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -535,8 +548,12 @@ def run_bucket(case, inp, dev, per_receiver_walk_ms, reps=3, extra_flags=0,
     J = torch.empty((A, nb), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     flags = t2.ASYNC | t2.BUCKET | extra_flags
+    w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0.record(stream)
     tree.J(inp["active"], case["nside"], case["theta"], out=J, flags=flags)
+    w1.record(stream)
     torch.cuda.synchronize()
+    first_ms = w0.elapsed_time(w1)  # includes tables built on first use
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(reps):
@@ -546,7 +563,7 @@ def run_bucket(case, inp, dev, per_receiver_walk_ms, reps=3, extra_flags=0,
     tree.status()
     ms = e0.elapsed_time(e1) / reps
     out = {"walk_ms": ms, "units_per_s": A * npix * nb / (ms * 1e-3), "unit": UNIT,
-           "kernel": kernel, "flags": flags & ~t2.ASYNC,
+           "kernel": kernel, "flags": flags & ~t2.ASYNC, "first_call_ms": first_ms,
            "speedup_vs_per_receiver": per_receiver_walk_ms / ms,
            "_J": J.cpu().numpy()}
     tree.free()

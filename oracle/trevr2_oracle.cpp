@@ -585,6 +585,26 @@ bool ray_chord(const double x[3], const double n[3], const double blo[3], const 
   return t1 > t0;
 }
 
+template <class F>
+void parallel_for(int64_t n, int nthreads, F&& f) {
+  if (nthreads <= 0) nthreads = static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
+  if (nthreads == 1 || n < 2) {
+    for (int64_t i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int64_t> next(0);
+  std::vector<std::thread> pool;
+  for (int w = 0; w < nthreads; ++w)
+    pool.emplace_back([&]() {
+      for (;;) {
+        int64_t i = next.fetch_add(1);
+        if (i >= n) break;
+        f(i);
+      }
+    });
+  for (auto& th : pool) th.join();
+}
+
 enum : uint32_t { FLAG_SOFT = 1u, FLAG_THICK = 2u, FLAG_LINEAR = 8u, FLAG_BUCKET = 16u,
                   FLAG_PP = 32u, FLAG_CSM = 64u };
 
@@ -611,14 +631,17 @@ CsmTables csm_tables(const Tree& t, const Aggregates<double>& ag, const std::vec
   }
   cs.d.assign(n * npix, 0.0);
   cs.tau.assign(n * npix * nb, 0.0);
-  for (int64_t q = n - 1; q >= 0; --q) {
+  // directions are independent: one worker per direction, cells from the
+  // leaves up (children come after their parent in breadth-first order)
+  parallel_for(npix, 0, [&](int64_t k) {
+   const double* nk = &dirs[3 * k];
+   for (int64_t q = n - 1; q >= 0; --q) {
     if (!(ag.Ltot[q] > 0.0)) continue;
     const Node& nd = t.nodes[q];
     double lo[3], hi[3];
     node_box(nd, t.lo, t.size, lo, hi);
     const double* c = &ag.c[3 * q];
-    for (int64_t k = 0; k < npix; ++k) {
-      const double* nk = &dirs[3 * k];
+    {
       double t0, t1;
       const double d = ray_chord(c, nk, lo, hi, t0, t1) ? t1 : 0.0;
       cs.d[q * npix + k] = d;
@@ -655,7 +678,8 @@ CsmTables csm_tables(const Tree& t, const Aggregates<double>& ag, const std::vec
       for (int b = 0; b < nb; ++b)
         tq[b] = ag.L[q * nb + b] > 0.0 ? -std::log(sum[b] / ag.L[q * nb + b]) : 0.0;
     }
-  }
+   }
+  });
   return cs;
 }
 
@@ -949,25 +973,6 @@ Problem<T> make_problem(const Tree& t, const Aggregates<T>& ag, const std::vecto
   return pr;
 }
 
-template <class F>
-void parallel_for(int64_t n, int nthreads, F&& f) {
-  if (nthreads <= 0) nthreads = static_cast<int>(std::max(1u, std::thread::hardware_concurrency()));
-  if (nthreads == 1 || n < 2) {
-    for (int64_t i = 0; i < n; ++i) f(i);
-    return;
-  }
-  std::atomic<int64_t> next(0);
-  std::vector<std::thread> pool;
-  for (int w = 0; w < nthreads; ++w)
-    pool.emplace_back([&]() {
-      for (;;) {
-        int64_t i = next.fetch_add(1);
-        if (i >= n) break;
-        f(i);
-      }
-    });
-  for (auto& th : pool) th.join();
-}
 
 // R11: r_pp and the p-p particles of every bucket that holds a receiver.
 template <class T>
