@@ -40,7 +40,7 @@ namespace trevr2 {
 // depth towards the bucket (direction -n_k) to the beam's.
 template <int NBP>
 __device__ __forceinline__ void add_csm(const WalkArgs& a, int ref, int k, BandVec<NBP>& tk) {
-  if (!a.csm_tau || (ref & kRefElement)) return;
+  if (ref & kRefElement) return;
   const BandVec<NBP> c =
       load_bands<NBP>(a.csm_tau + (int64_t(ref) * a.npix + a.csm_anti[k]) * NBP);
 #pragma unroll
@@ -54,7 +54,7 @@ __device__ __forceinline__ void add_csm(const WalkArgs& a, int ref, int k, BandV
 // crossed far halves go on the stack.  The stack walk then takes the far
 // halves, nearest first.  This visits the same cells in the same order as a
 // walk from the root.
-template <int NBP, bool kBucket = false, bool kPP = false>
+template <int NBP, bool kBucket = false, bool kPP = false, bool kCSM = false>
 __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int* lstk,
                              const SrcEntry* V, float* T, const int* off, const int* order,
                              int nbeams, int* next_beam, const NodeW* chain, int leaf,
@@ -94,7 +94,7 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
         BandVec<NBP> tk;
 #pragma unroll
         for (int b = 0; b < NBP; ++b) tk.v[b] = tau[b] + al.v[b] * ds;
-        if constexpr (kBucket) add_csm<NBP>(a, V[ptr].ref, k, tk);
+        if constexpr (kCSM) add_csm<NBP>(a, V[ptr].ref, k, tk);
         store_bands<NBP>(T + int64_t(ptr) * NBP, tk);
         ++ptr;
         s_next = ptr < end ? V[ptr].s : INFINITY;
@@ -149,7 +149,7 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
 #pragma unroll
     for (int b = 0; b < NBP; ++b) tk.v[b] = tau[b];
     for (; ptr < end; ++ptr) {
-      if constexpr (kBucket) {
+      if constexpr (kCSM) {
         BandVec<NBP> tc = tk;
         add_csm<NBP>(a, V[ptr].ref, k, tc);
         store_bands<NBP>(T + int64_t(ptr) * NBP, tc);
@@ -561,8 +561,9 @@ __device__ __forceinline__ void eval_bucket(const WalkArgs& a, bool soft, int la
 }
 
 // J of the receivers in slots [p0, p1), all in leaf q, into their rows
-// (kPP: with the p-p absorption of Sec. 2.4).
-template <int NBP, bool kPP>
+// (kPP: with the p-p absorption of Sec. 2.4; kCSM: with the complex source
+// model of Sec. 2.7).
+template <int NBP, bool kPP, bool kCSM>
 __device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0, int64_t p1,
                             int q, int64_t gw, int lane, int* stk, int* off, int* next_beam,
                             int* lstk, SrcEntry* U, int* Up, SrcEntry* V, float* T) {
@@ -632,15 +633,15 @@ __device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0,
       const int total = phase_sources<true, kPP>(a, o, si_o, lane, stk, a.stack_ints, U, Up, lo,
                                                  rpp);
       const int staged = min(total - lo, a.M);
-      make_sources<true>(a, o, si_o, lane, U, Up, staged);
+      make_sources<true, kCSM>(a, o, si_o, lane, U, Up, staged);
       const int n = staged > 0 ? bin_sources(a, lane, U, Up, staged, V, off) : 0;
       if (n > 0) {
         int* order = off + a.npix;
         const int nbeams = order_beams(a, lane, V, off, order, order + a.npix);
         if (lane == 0) *next_beam = 32;
         __syncwarp();
-        phase_absorb<NBP, true, kPP>(a, o, si_o, lane, lstk, V, T, off, order, nbeams,
-                                     next_beam, chain, leaf, rpp);
+        phase_absorb<NBP, true, kPP, kCSM>(a, o, si_o, lane, lstk, V, T, off, order, nbeams,
+                                           next_beam, chain, leaf, rpp);
         __syncwarp();
         eval_bucket<NBP, kPP>(a, soft, lane, V, T, n, nrec, xr, hr, si, acc, npp, ppxh, ppkc,
                               ppsi, ppw);
@@ -669,7 +670,7 @@ __device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0,
 }
 
 // One warp per bucket; slots from a global counter.
-template <int NBP, int WARPS, bool kPP>
+template <int NBP, int WARPS, bool kPP, bool kCSM>
 __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS)
     k_walk_bucket(WalkArgs a, const __grid_constant__ BucketArgs bk) {
   extern __shared__ int smem[];
@@ -704,7 +705,8 @@ __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS)
       p1 += __ffs(~same) - 1;
       break;
     }
-    walk_bucket<NBP, kPP>(a, bk, p0, p1, q, gw, lane, stk, off, next_beam, lstk, U, Up, V, T);
+    walk_bucket<NBP, kPP, kCSM>(a, bk, p0, p1, q, gw, lane, stk, off, next_beam, lstk, U, Up, V,
+                                T);
   }
 }
 
@@ -1116,9 +1118,12 @@ static int ensure_csm(Tree* t, Table* tb, cudaStream_t st) {
 }
 
 template <int NBP>
-static const void* bucket_kernel_nbp(bool pp) {
-  return pp ? reinterpret_cast<const void*>(&k_walk_bucket<NBP, kWalkWarps, true>)
-            : reinterpret_cast<const void*>(&k_walk_bucket<NBP, kWalkWarps, false>);
+static const void* bucket_kernel_nbp(bool pp, bool csm) {
+  if (csm)
+    return pp ? reinterpret_cast<const void*>(&k_walk_bucket<NBP, kWalkWarps, true, true>)
+              : reinterpret_cast<const void*>(&k_walk_bucket<NBP, kWalkWarps, false, true>);
+  return pp ? reinterpret_cast<const void*>(&k_walk_bucket<NBP, kWalkWarps, true, false>)
+            : reinterpret_cast<const void*>(&k_walk_bucket<NBP, kWalkWarps, false, false>);
 }
 
 // p-p particles one warp holds for a bucket (TREVR2_PP); a bucket whose
@@ -1177,8 +1182,10 @@ static int launch_walk_bucket(Tree* t, Table* tb, const int64_t* active, int64_t
   bk.mass = t->mass;
   bk.directed = target != nullptr;
   for (int c = 0; c < 3; ++c) bk.target[c] = target ? (target[c] - t->lo[c]) / t->size : 0.0;
-  const void* fn = t->nbp == 1 ? bucket_kernel_nbp<1>(bk.pp)
-                 : t->nbp == 2 ? bucket_kernel_nbp<2>(bk.pp) : bucket_kernel_nbp<4>(bk.pp);
+  const bool csm = (flags & TREVR2_CSM) != 0;
+  const void* fn = t->nbp == 1 ? bucket_kernel_nbp<1>(bk.pp, csm)
+                 : t->nbp == 2 ? bucket_kernel_nbp<2>(bk.pp, csm)
+                               : bucket_kernel_nbp<4>(bk.pp, csm);
   const size_t smem = walk_smem(kWalkWarps, a.stack_ints, a.npix, a.max_depth);
   int per_sm = 0, sms = 0;
   T2_CHECK(config_walk_kernel(fn, kWalkWarps, smem, &per_sm, &sms));

@@ -288,7 +288,7 @@ static __device__ float soft_kernel(float r, float h) {
 // a source on top of the receiver (r == 0) or with s <= 0.  From a bucket
 // centre (kBucket) r/s is the centre's and goes unused and there is no
 // kernel: each receiver of the bucket applies its own distance.
-template <bool kBucket = false>
+template <bool kBucket = false, bool kCSM = false>
 __device__ __forceinline__ bool make_source(const WalkArgs& a, float3 p, const double* p64,
                                             float3 x, int si, int ref, SrcEntry& out, int& pix) {
   const float vx = p.x - x.x, vy = p.y - x.y, vz = p.z - x.z;
@@ -315,9 +315,11 @@ __device__ __forceinline__ bool make_source(const WalkArgs& a, float3 p, const d
     // source model (Sec. 2.7) a cell's source takes the beam only up to its
     // projected edge s - d, d its own ray back towards the bucket
     out.w = s;
-    if (a.csm_tau && !(ref & kRefElement)) {
-      const float d = a.csm_d[int64_t(ref) * a.npix + a.csm_anti[k]];
-      out.s = fmaxf(s - d, 1e-30f);
+    if constexpr (kCSM) {
+      if (!(ref & kRefElement)) {
+        const float d = a.csm_d[int64_t(ref) * a.npix + a.csm_anti[k]];
+        out.s = fmaxf(s - d, 1e-30f);
+      }
     }
   } else {
     out.w = (a.flags & TREVR2_SOFT) ? soft_kernel(r, a.hn[si]) : 1.0f / (kFourPi * r2);
@@ -410,7 +412,7 @@ static __device__ int phase_sources(const WalkArgs& a, float3 x, int si, int lan
 // The records of the n staged sources, all lanes at once: beam, projected
 // distance, r/s, kernel (make_source); a source the method skips (r = 0, or
 // not in front of its beam) gets beam -1.
-template <bool kBucket = false>
+template <bool kBucket = false, bool kCSM = false>
 static __device__ void make_sources(const WalkArgs& a, float3 x, int si, int lane, SrcEntry* U,
                                     int* Up, int n) {
   for (int e = lane; e < n; e += 32) {
@@ -429,7 +431,7 @@ static __device__ void make_sources(const WalkArgs& a, float3 x, int si, int lan
     }
     SrcEntry ent;
     int pix = -1;
-    if (make_source<kBucket>(a, p, p64, x, si, ref, ent, pix)) U[e] = ent; else pix = -1;
+    if (make_source<kBucket, kCSM>(a, p, p64, x, si, ref, ent, pix)) U[e] = ent; else pix = -1;
     Up[e] = pix;
   }
   __syncwarp();
