@@ -64,3 +64,34 @@ def test_python_layer_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(t2, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         t2.load_library()
+
+
+def test_flag_values_agree(lib):
+    """The header's flag bits, the Python binding's constants and the
+    oracle's flags are the same numbers."""
+    import os
+    import re
+
+    import oracle
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "include", "trevr2.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in
+            re.finditer(r"#define TREVR2_([A-Z]+) (\d+)u", hdr)}
+    for name in ("SOFT", "THICK", "ASYNC", "LINEAR", "BUCKET", "PP", "CSM"):
+        assert getattr(lib, name) == defs[name], name
+    for name in ("SOFT", "THICK", "LINEAR", "BUCKET", "PP", "CSM"):
+        assert getattr(oracle, "FLAG_" + name) == defs[name], name
+    bits = [defs[n] for n in ("SOFT", "THICK", "ASYNC", "LINEAR", "BUCKET", "PP", "CSM")]
+    assert len(set(bits)) == len(bits) and all(b & (b - 1) == 0 for b in bits)
+
+
+def test_new_entry_points_validate_on_host(lib):
+    so = lib.load_library()
+    assert so.trevr2_set_tau_refine(None, ctypes.c_double(0.1), None) == -1
+    assert b"tree is NULL" in so.trevr2_last_error()
+    tgt = (ctypes.c_double * 3)(0.5, 0.5, 0.5)
+    assert so.trevr2_J_directed(None, None, 0, 2, ctypes.c_float(0.75), None, 0, 16, tgt,
+                                None, None) == -1
+    assert so.trevr2_J_directed(None, None, 0, 2, ctypes.c_float(0.75), None, 0, 16, None,
+                                None, None) == -1
+    assert b"target is NULL" in so.trevr2_last_error()
