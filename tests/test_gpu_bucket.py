@@ -171,3 +171,21 @@ def test_bucket_accuracy_geometries(t2, oracle_mod, name):
     e_o, c_o = esc.figures(ref, pts, g)
     assert abs(e - e_o) <= 1e-5 * e_o and abs(c - c_o) <= 2.0 / len(act)
     tree.free()
+
+
+@pytest.mark.parametrize("extra", [0, 32 | 2, 64])
+def test_bucket_rows_do_not_depend_on_the_other_receivers(t2, extra):
+    """A receiver's J comes from its bucket's walk alone: the rows of any
+    subset of receivers, in any order, equal those of the full walk bit for
+    bit (what makes Morton-range sharding exact)."""
+    case = workloads.random_case(3000, 60, nb=2, seed=111, clumped=True)
+    tree = _gpu_tree(t2, case)
+    flags = BUCKET | extra
+    act = case["active"]
+    J = tree.J(act, 2, 0.75, flags=flags).cpu().numpy()
+    rng = np.random.default_rng(9)
+    for m in (1, 37, 1000):
+        sub = rng.choice(len(act), m, replace=False)
+        Js = tree.J(act[sub], 2, 0.75, flags=flags).cpu().numpy()
+        np.testing.assert_array_equal(Js, J[sub])
+    tree.free()

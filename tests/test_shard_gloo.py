@@ -39,6 +39,30 @@ def _inv(ot):
     return inv
 
 
+def _bucket_worker(rank, world, port, queue):
+    """Per-bucket beams with p-p absorption and the complex source model: a
+    receiver's J depends on its bucket only, so Morton ranges walked on
+    different ranks give the rows of one walk over all receivers."""
+    import torch.distributed as dist
+
+    import oracle
+    from paper_2310_15235_gb300 import shard
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    try:
+        case = _case()
+        ot = oracle.OracleTree.from_case(case)
+        act = case["active"]
+        order = shard.morton_rank(_inv(ot), act)
+        flags = oracle.FLAG_BUCKET | oracle.FLAG_PP | oracle.FLAG_CSM
+        J = shard.J_sharded(order, act, lambda a: torch.from_numpy(
+            ot.J(a, NSIDE, THETA, flags=flags)))
+        queue.put((rank, J.numpy()))
+    finally:
+        dist.destroy_process_group()
+
+
 def _worker(rank, world, port, queue):
     import torch.distributed as dist
 
@@ -112,3 +136,23 @@ def test_sharded_J_and_gradient_world2(oracle_mod):
     for rank, J, g, _ in results:
         np.testing.assert_array_equal(J, J_full)  # gathered rows land in place
         np.testing.assert_allclose(g, g_full, rtol=1e-12, atol=1e-15 * np.abs(g_full).max())
+
+
+def test_sharded_bucket_J_world2(oracle_mod):
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    queue = ctx.Queue()
+    procs = [ctx.Process(target=_bucket_worker, args=(r, world, port, queue))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    results = [queue.get(timeout=300) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    case = _case()
+    ot = oracle_mod.OracleTree.from_case(case)
+    flags = oracle_mod.FLAG_BUCKET | oracle_mod.FLAG_PP | oracle_mod.FLAG_CSM
+    J_full = ot.J(case["active"], NSIDE, THETA, flags=flags)
+    for _, J in results:
+        np.testing.assert_array_equal(J, J_full)
