@@ -8,6 +8,13 @@ There is no CPU fallback; without the library every call raises.
     tree = build(pos, mass, kappa, lum, h=None)    # Sec. 2.3 / 2.6
     J = tree.J(active, nside=2, theta=0.75)        # Sec. 2.5, [A, nb] float32
 
+The paper's other schemes are flags of J: BUCKET (one walk per bucket from
+its centre, Sec. 2.5.1) with PP (p-p absorption inside r_pp, Sec. 2.4) and
+CSM (the complex source model, Sec. 2.7); LINEAR (the linear absorption
+average of Sec. 2.6); SOFT and THICK (Eq. intint, Eq. taucorr).
+``tree.J(..., target=p)`` aims the beam holding p at it (directed rays,
+Sec. 3.4.1) and ``tree.set_tau_refine(t)`` turns on absorption refinement.
+
 Tensors may live on the GPU (used in place) or on the host (copied to the
 current CUDA device first; the result stays on the device).
 """
