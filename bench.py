@@ -629,15 +629,16 @@ def run_walk_only(args):
         e0.record()
         tree.J(inp["active"], case["nside"], case["theta"], out=J,
                flags=t2.ASYNC | (t2.BUCKET if args.bucket else 0)
-               | (t2.BUCKET | t2.PP | t2.THICK if args.pp else 0))
+               | (t2.BUCKET | t2.PP | t2.THICK if args.pp else 0)
+               | (t2.BUCKET | t2.CSM if args.csm else 0))
         e1.record()
         torch.cuda.synchronize()
         if k >= args.warmup:
             times.append(e0.elapsed_time(e1))
     tree.status()
     ms = float(np.mean(times))
-    print(json.dumps({"mode": "walk-only", "bucket": bool(args.bucket or args.pp),
-                      "pp": bool(args.pp), "lattice": n,
+    print(json.dumps({"mode": "walk-only", "bucket": bool(args.bucket or args.pp or args.csm),
+                      "pp": bool(args.pp), "csm": bool(args.csm), "lattice": n,
                       "receivers": A, "walk_ms": ms,
                       "units_per_s": A * npix * nb / (ms * 1e-3), "nodes": tree.n_nodes,
                       "max_depth": tree.max_depth}), flush=True)
@@ -661,6 +662,8 @@ def main():
     ap.add_argument("--pp", action="store_true",
                     help="with --walk-only: per-bucket beams with p-p absorption and "
                          "TREVR2_THICK")
+    ap.add_argument("--csm", action="store_true",
+                    help="with --walk-only: per-bucket beams with the complex source model")
     ap.add_argument("--no-bucket", action="store_true",
                     help="skip the per-bucket beams measurement")
     ap.add_argument("--no-batched", action="store_true",
