@@ -7,7 +7,10 @@
 // HEALPix beams (Sec. 1.3, Sec. 2.5), the cell opening criterion B/d > theta
 // (Sec. 2.5.2), the per-beam optical depth with the projected-distance
 // correction (Sec. 2.5.1), and the optional finite-size (Eq. intint) and
-// optically-thick (Eq. taucorr) factors.  Only the tests, the smoke check and
+// optically-thick (Eq. taucorr) factors; with flags, the per-bucket walk
+// (Sec. 2.5), particle-particle absorption (Sec. 2.4), the complex source
+// model (Sec. 2.7), linear averaging (Sec. 2.6), directed rays (Sec. 3.4.1)
+// and absorption refinement (Sec. 2.5.2).  Only the tests, the smoke check and
 // the CPU baseline of the benchmark may load it; the product library never
 // does, and the two share no code, headers or tables.
 //

@@ -286,8 +286,10 @@ static __device__ float soft_kernel(float r, float h) {
 
 // Bin one source: beam, projected distance, r/s, kernel.  Returns false for
 // a source on top of the receiver (r == 0) or with s <= 0.  From a bucket
-// centre (kBucket) r/s is the centre's and goes unused and there is no
-// kernel: each receiver of the bucket applies its own distance.
+// centre (kBucket) there is no kernel and r/s is the centre's, unused: w
+// holds the projected distance s, each receiver of the bucket applies its
+// own distance, and with kCSM the absorption key s moves to the cell's
+// projected edge.
 template <bool kBucket = false, bool kCSM = false>
 __device__ __forceinline__ bool make_source(const WalkArgs& a, float3 p, const double* p64,
                                             float3 x, int si, int ref, SrcEntry& out, int& pix) {
