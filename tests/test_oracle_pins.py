@@ -1082,3 +1082,30 @@ def test_csm_closed_form_one_source(oracle_mod, nside, theta):
     np.testing.assert_allclose(J[ok], J0[ok], rtol=1e-12)
     with pytest.raises(ValueError):
         t.J(case["active"][:3], nside, theta, flags=oracle_mod.FLAG_CSM)
+
+
+def test_pp_source_does_not_absorb_its_own_light(oracle_mod):
+    """A luminous gas element with mass and opacity, the receiver and nothing
+    else, all in one bucket: the source is not a p-p absorber of its own
+    light (nor is the receiver of what it receives), so J = L / (4 pi r^2)
+    exactly; a third gas element on the segment attenuates as usual."""
+    flags = oracle_mod.FLAG_BUCKET | oracle_mod.FLAG_PP
+    pos = np.array([[0.3, 0.5, 0.5], [0.7, 0.5, 0.5], [0.9, 0.9, 0.9]])
+    mass = np.array([2e-3, 2e-3, 2e-3])
+    kappa = np.array([[40.0], [40.0], [0.0]])
+    lum = np.array([[0.0], [1.0], [0.0]])
+    case = workloads._pack("pp_self", pos, mass, kappa, lum, np.full(3, 0.1), np.array([0]),
+                           2, 0.75, bucket=12)
+    t = oracle_mod.OracleTree.from_case(case)
+    J = t.J([0], 2, 0.75, flags=flags)[0, 0]
+    assert J == pytest.approx(1.0 / (4 * np.pi * 0.4 ** 2), rel=1e-14)
+    # move the third element onto the segment: it attenuates
+    pos[2] = [0.5, 0.5, 0.5]
+    kappa[2] = 40.0
+    case = workloads._pack("pp_self2", pos, mass, kappa, lum, np.full(3, 0.1), np.array([0]),
+                           2, 0.75, bucket=12)
+    t = oracle_mod.OracleTree.from_case(case)
+    h, m, k = float(case["h"][2]), float(case["mass"][2]), float(case["kappa"][2, 0])
+    J = t.J([0], 2, 0.75, flags=flags)[0, 0]
+    assert J == pytest.approx(np.exp(-k * 3 * m / (np.pi * h * h)) / (4 * np.pi * 0.4 ** 2),
+                              rel=1e-13)
