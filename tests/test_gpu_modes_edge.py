@@ -98,3 +98,17 @@ def test_refinement_with_pp_and_csm(t2, oracle_mod, tau):
     J = tree.J(case["active"], 2, 0.75, flags=flags).cpu().numpy()
     _assert_J(J, ot.J(case["active"], 2, 0.75, flags=flags), f"refine {tau}")
     tree.free()
+
+
+@pytest.mark.parametrize("nside", [8, 16])
+@pytest.mark.parametrize("flags", [BUCKET, BUCKET | PP | THICK, BUCKET | CSM])
+def test_modes_at_the_largest_nside(t2, oracle_mod, nside, flags):
+    """768 and 3072 beams: the walk's shared-memory layout, the p-p sphere
+    (r_pp = h / sqrt(4 pi / N_ray) holds every particle here) and the complex
+    source tables at their largest."""
+    case = workloads.random_case(600, 20, nb=2, seed=204, clumped=True, n_active=150)
+    tree = _gpu_tree(t2, case)
+    J = tree.J(case["active"], nside, 0.75, flags=flags).cpu().numpy()
+    ref = oracle_mod.OracleTree.from_case(case).J(case["active"], nside, 0.75, flags=flags)
+    _assert_J(J, ref, f"nside={nside} flags={flags}")
+    tree.free()
