@@ -167,3 +167,23 @@ def test_refined_accuracy_rows(t2, oracle_mod, name, directed):
     dc = 0.005 if name == "source_two_clouds" else 0.03
     assert abs(e - want[0]) <= 0.003 and abs(c - want[1]) <= max(dc, 0.005), (e, c, want)
     tree.free()
+
+
+def test_refined_noalloc_equals_refined_J(t2):
+    """The allocation-free entry point walks the same refined node copy: its
+    rows equal trevr2_J's to FP32 rounding (it stages 256 sources per pass
+    instead of 1024, so its sums split differently)."""
+    import ctypes as C
+    case = workloads.random_case(1500, 30, nb=2, seed=178, clumped=True)
+    tree = _gpu_tree(t2, case)
+    tree.set_tau_refine(0.05)
+    J = tree.J(case["active"], 2, 0.75).cpu().numpy()
+    lib = t2.load_library()
+    act = torch.as_tensor(case["active"], dtype=torch.int64, device="cuda")
+    out = torch.full((act.numel(), 2), -1.0, dtype=torch.float32, device="cuda")
+    rc = lib.trevr2_J_noalloc(tree._h, C.c_void_p(act.data_ptr()), act.numel(), 2,
+                              C.c_float(0.75), None, 2, 0, C.c_void_p(out.data_ptr()),
+                              C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, t2.load_library().trevr2_last_error()
+    np.testing.assert_allclose(out.cpu().numpy(), J, rtol=2e-6, atol=0)
+    tree.free()
