@@ -1109,3 +1109,57 @@ def test_pp_source_does_not_absorb_its_own_light(oracle_mod):
     J = t.J([0], 2, 0.75, flags=flags)[0, 0]
     assert J == pytest.approx(np.exp(-k * 3 * m / (np.pi * h * h)) / (4 * np.pi * 0.4 ** 2),
                               rel=1e-13)
+
+
+def test_csm_equals_plain_walk_on_the_beam_line(oracle_mod):
+    """A luminous, absorbing star exactly on a pixel-centre beam from the
+    receiver's bucket centre, alone in a leaf that the cut accepts: the
+    beam and the star's ray back towards the bucket are one line, so the
+    complex source model (beam cut at the star's projected edge s - d, plus
+    the leaf's alpha times d on the ray towards the bucket) gives the plain
+    walk's optical depth exactly.  The ray away from the bucket would not."""
+    rng = np.random.default_rng(211)
+    idx = np.arange(8, dtype=np.float64)
+    grid = (np.stack(np.meshgrid(idx, idx, idx, indexing="ij"), -1).reshape(-1, 3) + 0.5) / 8
+    n_g = len(grid)
+    recv = int(np.flatnonzero(np.all(np.isclose(grid, [1.5 / 8, 1.5 / 8, 1.5 / 8]), axis=1))[0])
+    dirs = oracle_mod.pix2vec(2)
+    k = int(np.argmax(dirs @ np.array([1.0, 1.0, 1.0])))  # a beam into the box
+    star = grid[recv] + 0.48 * dirs[k]  # nearer its leaf's face towards the receiver
+    assert np.all((star > 0) & (star < 1))
+    pos = np.concatenate([grid, star[None, :]])
+    n = len(pos)
+    mass = np.concatenate([rng.uniform(0.5, 1.5, n_g) / n_g, [1.0 / n_g]])
+    kappa = np.concatenate([rng.uniform(1.0, 20.0, (n_g, 1)), [[30.0]]])
+    lum = np.zeros((n, 1))
+    lum[-1] = 1.0
+    case = workloads._pack("beam_line", pos, mass, kappa, lum, np.full(n, 1 / 8),
+                           np.array([recv]), 2, 0.75, bucket=1)
+    t = oracle_mod.OracleTree.from_case(case)
+    e, ag = t.export(), t.aggregates()
+    centres = _leaf_centres(t, n)
+    np.testing.assert_array_equal(centres[recv], grid[recv])
+    # the star's leaf and its parent; theta between their B/d makes the cut
+    # accept the leaf and open every ancestor
+    leaf = int(np.flatnonzero((e["child"] < 0) & (e["count"] == 1)
+                              & np.isin(e["first"], np.flatnonzero(e["perm"] == n - 1)))[0])
+    parent = int(e["parent"][leaf])
+
+    def dist(q):
+        lo, hi = e["box"][q, :3], e["box"][q, 3:]
+        return np.linalg.norm(np.maximum(0, np.maximum(lo - grid[recv], grid[recv] - hi)))
+
+    lo_t, hi_t = ag["B"][leaf] / dist(leaf), ag["B"][parent] / dist(parent)
+    assert lo_t < hi_t
+    theta = 0.5 * (lo_t + hi_t)
+    J_plain = t.J([recv], 2, theta, flags=oracle_mod.FLAG_BUCKET)[0, 0]
+    J_csm = t.J([recv], 2, theta, flags=oracle_mod.FLAG_BUCKET | oracle_mod.FLAG_CSM)[0, 0]
+    assert J_plain > 0
+    assert J_csm == pytest.approx(J_plain, rel=1e-12)
+    # the leaf absorbs along the line, and the star sits near the face towards
+    # the receiver: its ray away from the bucket is the longer one, so taking
+    # it would cut the beam before the leaf and drop absorption there
+    d, tau = t.csm_tables(2)
+    anti = int(oracle_mod.vec2pix(2, -dirs[k][None, :])[0])
+    assert tau[leaf, anti, 0] > 1e-3
+    assert d[leaf, k] > 2.0 * d[leaf, anti]
