@@ -14,7 +14,7 @@ Escape fraction and covering factor follow the definitions of Table escape:
 the escape fraction is the flux that reaches the outer sphere relative to an
 unabsorbed source, i.e. the solid-angle mean of J / J_vac with J_vac the J of
 the same sources in vacuum; the covering factor is the fraction of the
-sphere's solid angle where J is at most half of the J seen without the
+sphere's solid angle where J is less than half of the J seen without the
 features (background absorption only).  On a shell of receivers that sample
 solid angle evenly both are plain means over the receivers.
 """
@@ -100,8 +100,9 @@ def escape_fraction(J, J_vac):
 
 
 def covering_factor(J, J_nofeatures):
-    """Fraction of receivers where J <= J_nofeatures / 2."""
-    return float(np.mean(np.asarray(J, np.float64) <= 0.5 * np.asarray(J_nofeatures, np.float64)))
+    """Fraction of receivers where J < J_nofeatures / 2 (less than half of
+    the flux without the features arrives)."""
+    return float(np.mean(np.asarray(J, np.float64) < 0.5 * np.asarray(J_nofeatures, np.float64)))
 
 
 def sphere_points(n, centre, radius):
