@@ -1163,3 +1163,103 @@ def test_csm_equals_plain_walk_on_the_beam_line(oracle_mod):
     anti = int(oracle_mod.vec2pix(2, -dirs[k][None, :])[0])
     assert tau[leaf, anti, 0] > 1e-3
     assert d[leaf, k] > 2.0 * d[leaf, anti]
+
+
+def _two_star_root(seed, stars, lums):
+    """Seven gas elements in each x half of the unit cube plus one star in
+    each: the root splits once (16 elements, bucket 12) into two leaves, a
+    star in each."""
+    rng = np.random.default_rng(seed)
+    lower = rng.uniform([0.02, 0.02, 0.02], [0.48, 0.98, 0.98], (7, 3))
+    upper = rng.uniform([0.52, 0.02, 0.02], [0.98, 0.98, 0.98], (7, 3))
+    pos = np.concatenate([lower, upper, np.asarray(stars, np.float64)])
+    n = len(pos)
+    # very different opacity in the two halves, so that the two stars' rays
+    # have very different optical depths
+    kappa = np.concatenate([rng.uniform(0.5, 2.0, (7, 2)), rng.uniform(40.0, 80.0, (7, 2)),
+                            np.zeros((2, 2))])
+    mass = np.concatenate([rng.uniform(0.5, 1.5, 14) / 14, [0.0, 0.0]])
+    lum = np.zeros((n, 2))
+    lum[14:] = lums
+    return workloads._pack("two_star_root", pos, mass, kappa, lum, np.full(n, 0.2),
+                           np.arange(14), 2, 0.75, bucket=12)
+
+
+@pytest.mark.parametrize("seed,stars,lums", [
+    # a bright star high in the lower half, a faint one low in the upper
+    # half: oblique rays of the root end early, at its top face, and the
+    # plane clips the upper star's ray inside its own leaf
+    (191, [[0.05, 0.99, 0.5], [0.55, 0.10, 0.5]], [[1.0, 0.2], [0.1, 0.6]]),
+    # both stars near the split plane: their rays extend through the sibling
+    (192, [[0.40, 0.35, 0.62], [0.58, 0.70, 0.31]], [[0.3, 1.0], [1.0, 0.25]]),
+    (193, [[0.21, 0.83, 0.12], [0.91, 0.27, 0.77]], [[0.7, 0.7], [0.4, 0.9]]),
+])
+def test_csm_two_stars_combine_by_srccomb(oracle_mod, seed, stars, lums):
+    """Two luminous children (Sec. 2.7, Eq. srccomb): the root's ray in
+    direction k ends on the plane through the end of its own ray (from its
+    centre of luminosity to its box edge), perpendicular to n_k.  Each star
+    is attenuated along its own straight line to that plane, and the root
+    keeps the optical depth of the summed attenuated luminosity,
+    L e^{-tau} = sum_i L_i e^{-tau_i'}.  Every tau_i' here is a point-sampled
+    line integral of the two buckets' alpha (zero outside the root) from the
+    star to the plane, so the clip of a ray that reaches the plane inside its
+    own leaf, the extension through the sibling and the log of the sum are
+    all checked against the geometry itself.  A luminosity-weighted mean of
+    the tau_i', or the full leaf ray in place of the clipped one, misses."""
+    case = _two_star_root(seed, stars, lums)
+    t = oracle_mod.OracleTree.from_case(case)
+    e, ag = t.export(), t.aggregates()
+    assert e["child"][0] == 1 and np.all(e["child"][1:3] < 0)  # root and two leaves
+    lo, hi = e["box"][0, :3], e["box"][0, 3:]
+    star_pos = np.asarray(stars, np.float64)
+    Ls = case["lum"][14:].astype(np.float64)  # as stored (float32)
+    c = (Ls.sum(1)[:, None] * star_pos).sum(0) / Ls.sum()  # band-summed centre
+    np.testing.assert_allclose(ag["c"][0], c, rtol=1e-14)
+    mid = 0.5 * (lo[0] + hi[0])
+    leaf_of_star = [1 + int(p[0] >= mid) for p in star_pos]
+    assert sorted(leaf_of_star) == [1, 2]
+    n_clip = n_ext = 0
+    worst_mean = worst_noclip = 0.0
+    for nside in (1, 2, 4):
+        d, tau = t.csm_tables(nside)
+        dirs = oracle_mod.pix2vec(nside)
+        for k in range(len(dirs)):
+            nk = dirs[k]
+            dk = _exit_by_marching(c, nk, lo, hi)
+            assert d[0, k] == pytest.approx(dk, abs=1e-12)
+            end = c + dk * nk
+            taus, taus_full = [], []
+            for i, p in enumerate(star_pos):
+                D = max(0.0, float((end - p) @ nk))
+                m = 40000
+                ts = (np.arange(m) + 0.5) / m * D
+                pts = p[None, :] + ts[:, None] * nk[None, :]
+                inside = np.all((pts >= lo) & (pts < hi), axis=1)
+                leaf = 1 + (pts[:, 0] >= mid)
+                a = np.where(inside[:, None], ag["alpha_leaf"][leaf], 0.0)
+                taus.append(a.sum(0) * (D / m))
+                own = leaf == leaf_of_star[i]
+                # the star's own leaf ray runs on past the plane: the clip
+                d_own = _exit_by_marching(p, nk, e["box"][leaf_of_star[i], :3],
+                                          e["box"][leaf_of_star[i], 3:])
+                if 0.0 < D < d_own - 1e-6:
+                    n_clip += 1
+                    full = ag["alpha_leaf"][leaf_of_star[i]] * d_own
+                else:
+                    full = taus[-1]
+                taus_full.append(full)
+                if np.any(inside & ~own) and D > d_own + 1e-6:
+                    n_ext += 1
+            taus, taus_full = np.array(taus), np.array(taus_full)
+            want = -np.log((Ls * np.exp(-taus)).sum(0) / Ls.sum(0))
+            np.testing.assert_allclose(tau[0, k], want, rtol=5e-4, atol=1e-9)
+            # the planted alternatives land well away from the oracle
+            mean = (Ls * taus).sum(0) / Ls.sum(0)
+            noclip = -np.log((Ls * np.exp(-taus_full)).sum(0) / Ls.sum(0))
+            worst_mean = max(worst_mean, float(np.max(np.abs(mean - tau[0, k]))))
+            worst_noclip = max(worst_noclip, float(np.max(np.abs(noclip - tau[0, k]))))
+    assert n_ext > 0  # some rays reach the plane through the sibling
+    assert worst_mean > 0.05  # a weighted mean of tau is not Eq. srccomb
+    if seed == 191:
+        assert n_clip > 0
+        assert worst_noclip > 0.05  # the unclipped leaf ray is caught
