@@ -324,6 +324,13 @@ def run_ours(args, world, rank, local):
             extra["bucket"]["parity_sample"] = {"receivers": 256,
                                                 "median_rel": float(np.median(rel)),
                                                 "max_rel": float(rel.max())}
+            # a receiver's per-bucket counts are its bucket's walk
+            _, st_b = ot.J(sample[:256], case["nside"], case["theta"], flags=t2.BUCKET,
+                           nthreads=cores, stats=True)
+            per_walk, means_b = _algorithmic_bytes_per_receiver(st_b, nb)
+            per_eval = float(st_b[:, 3].mean()) * 16 + 4 * nb
+            extra["bucket"]["per_walk_counts"] = means_b
+            extra["_bucket_bytes"] = (per_walk, per_eval)
             # the paper's full near field: p-p absorption inside r_pp, the
             # receiver's own column by Eq. taucorr
             pp_flags = t2.PP | t2.THICK
@@ -380,18 +387,93 @@ def run_ours(args, world, rank, local):
         line["adjoint"]["clumpy_2M"] = run_adjoint_clumpy(case, inp, dev)
     if world == 1 and not args.no_batched:
         per_rec = roofline["algorithmic_bytes_per_unit"] * npix * nb if roofline else None
-        line["batched"] = run_batched(args, dev, per_rec, hbm_peak, peak_kind)
+        per_bucket, per_eval = extra.pop("_bucket_bytes", (None, None))
+        line["batched"] = run_batched(args, dev, per_rec, per_bucket, per_eval, hbm_peak,
+                                      peak_kind)
     line.update(extra)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
-def run_batched(args, dev, per_receiver_bytes, hbm_peak, peak_kind):
+def _leaf_lookup(tree):
+    """Maps receivers to the leaf holding them (each leaf is a contiguous
+    range of the tree's sorted elements)."""
+    perm = tree.export("perm").cpu().numpy()
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(len(perm), dtype=perm.dtype)
+    child = tree.export("child").cpu().numpy()
+    first = tree.export("first").cpu().numpy()
+    count = tree.export("count").cpu().numpy()
+    firsts = np.sort(first[(child < 0) & (count > 0)])
+    return lambda receivers: np.searchsorted(firsts, inv[receivers], side="right") - 1
+
+
+def _distinct_buckets(leaf_of, receivers):
+    return int(len(np.unique(leaf_of(receivers))))
+
+
+def _batched_arm(args, dev, trees, act, offsets, tree_of, members, outs, J, nside, theta, flags):
+    """One plan (autotuned, recorded in a CUDA graph, replayed) against one
+    plain trevr2_J launch per subset with the same flags on the same stream."""
+    import torch
+
+    import paper_2310_15235_gb300 as t2
+
+    stream = torch.cuda.current_stream()
+    plan = t2.Batch(trees, offsets, tree_of, nside=nside, theta=theta, flags=flags)
+    warps, staging = plan.autotune(act, J)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.run(act, J)
+    graph.replay()  # warm-up
+    torch.cuda.synchronize()
+    plan.status()
+    reps = max(1, args.batched_reps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plan.status()
+    batched_ms = e0.elapsed_time(e1) / reps
+    J_batched = J.clone()
+    plan.free()
+    del graph
+    big = int(np.argmax(np.diff(offsets)))
+    for t in range(len(trees)):  # walk buffers of every tree at their largest size
+        s = max((s for s in range(len(members)) if tree_of[s] == t),
+                key=lambda s: offsets[s + 1] - offsets[s])
+        trees[t].J(members[s], nside, theta, out=outs[s], flags=t2.ASYNC | flags)
+    trees[tree_of[big]].status()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        for s in range(len(members)):
+            if len(members[s]):
+                trees[tree_of[s]].J(members[s], nside, theta, out=outs[s],
+                                    flags=t2.ASYNC | flags)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    for tr in trees:
+        tr.status()
+    plain_ms = e0.elapsed_time(e1) / reps
+    same = bool(torch.equal(J, J_batched)) if staging == 1024 else None
+    return {"batched_ms": batched_ms, "plain_ms": plain_ms, "speedup_vs_plain": plain_ms / batched_ms,
+            "autotuned": {"warps_per_block": warps, "staged_sources_per_warp": staging},
+            "rows_equal_to_plain": same, "reps": reps}
+
+
+def run_batched(args, dev, per_receiver_bytes, per_bucket_walk_bytes, per_receiver_eval_bytes,
+                hbm_peak, peak_kind):
     """Individual-timestep batching (Sec. 1.2, Sec. 3.1): 4 snapshots of the
     clumpy 2M field, 64 subsets each of 10^U(2,6) receivers.  The batch is one
     autotuned persistent launch replayed from a CUDA graph; the comparison is
-    one plain trevr2_J launch per subset on the same stream."""
+    one plain trevr2_J launch per subset on the same stream with the same
+    flags.  Measured per receiver (the benchmark spec's walk) and per bucket
+    (TREVR2_BUCKET, the paper's own scheme, where a run walks each distinct
+    (snapshot, bucket) once)."""
     import torch
 
     import paper_2310_15235_gb300 as t2
@@ -414,72 +496,64 @@ def run_batched(args, dev, per_receiver_bytes, hbm_peak, peak_kind):
     total = int(offsets[-1])
     units = total * npix * nb
     J = torch.empty((total, nb), dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
-
-    plan = t2.Batch(trees, offsets, tree_of, nside=nside, theta=theta)
-    warps, staging = plan.autotune(act, J)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        plan.run(act, J)
-    graph.replay()  # warm-up
-    torch.cuda.synchronize()
-    plan.status()
-    reps = max(1, args.batched_reps)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        graph.replay()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    plan.status()
-    batched_ms = e0.elapsed_time(e1) / reps
-    J_batched = J.clone()
-
-    # plain: one trevr2_J launch per subset, in subset order, on one stream
     members = [act[offsets[s]:offsets[s + 1]] for s in range(len(subsets))]
     outs = [J[offsets[s]:offsets[s + 1]] for s in range(len(subsets))]
-    big = int(np.argmax(np.diff(offsets)))
-    for t in range(len(trees)):  # walk buffers of every tree at their largest size
-        s = max((s for s in range(len(subsets)) if tree_of[s] == t),
-                key=lambda s: offsets[s + 1] - offsets[s])
-        trees[t].J(members[s], nside, theta, out=outs[s], flags=t2.ASYNC)
-    trees[tree_of[big]].status()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(reps):
-        for s in range(len(subsets)):
-            if len(members[s]):
-                trees[tree_of[s]].J(members[s], nside, theta, out=outs[s], flags=t2.ASYNC)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    for tr in trees:
-        tr.status()
-    plain_ms = e0.elapsed_time(e1) / reps
-    same = bool(torch.equal(J, J_batched)) if staging == 1024 else None
-    distinct = sum(len(np.unique(np.concatenate([m for t, m in subsets if t == s])))
-                   for s in range(len(snaps)))
-    achieved = per_receiver_bytes * total / (batched_ms * 1e-3) / 1e9 if per_receiver_bytes else None
+    per_snap = [np.unique(np.concatenate([m for t, m in subsets if t == s]))
+                for s in range(len(snaps))]
+    distinct = sum(len(u) for u in per_snap)
+    leaf_of = [_leaf_lookup(tr) for tr in trees]
+    buckets = sum(_distinct_buckets(leaf_of[s], per_snap[s]) for s in range(len(snaps)))
+    plain_bucket_walks = sum(_distinct_buckets(leaf_of[t], m) for t, m in subsets if len(m))
+
+    rx = _batched_arm(args, dev, trees, act, offsets, tree_of, members, outs, J, nside, theta, 0)
+    bk = _batched_arm(args, dev, trees, act, offsets, tree_of, members, outs, J, nside, theta,
+                      t2.BUCKET)
+
+    def roof(nbytes, ms, counts, note):
+        if nbytes is None:
+            return None
+        achieved = nbytes / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_kind": peak_kind, "counts": counts,
+                "note": note}
+
     out = {
         "workload": "4 clumpy 2,097,152-element 3-band snapshots (seeds 1040-1043), 64 subsets "
                     "each of floor(10^U(2,6)) receivers drawn without replacement, nside 4, "
                     "theta 0.5",
         "subsets": len(subsets), "receivers": total, "units": units,
-        "batched_ms": batched_ms, "batched_units_per_s": units / (batched_ms * 1e-3),
-        "plain_ms": plain_ms, "plain_units_per_s": units / (plain_ms * 1e-3),
-        "speedup_vs_plain": plain_ms / batched_ms,
         "distinct_receivers": int(distinct),
         "launch": "one CUDA graph: row keys, radix sort, distinct (tree, receiver) keys, one "
                   "persistent walk kernel over the distinct ones, scatter to rows",
-        "autotuned": {"warps_per_block": warps, "staged_sources_per_warp": staging},
-        "plain_launches": int(sum(1 for m in members if len(m))), "reps": reps,
-        "rows_equal_to_plain": same,
-        "roofline": None if achieved is None else {
-            "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "peak_kind": peak_kind,
-            "note": "algorithmic bytes per receiver from the oracle's counts on the "
-                    "single-snapshot field (same generator and parameters)"},
+        "plain_launches": int(sum(1 for m in members if len(m))),
+        **rx,
+        "batched_units_per_s": units / (rx["batched_ms"] * 1e-3),
+        "plain_units_per_s": units / (rx["plain_ms"] * 1e-3),
+        "roofline": roof(None if per_receiver_bytes is None else per_receiver_bytes * distinct,
+                         rx["batched_ms"], "distinct (snapshot, receiver) walks",
+                         "algorithmic bytes per receiver walk from the oracle's counts on the "
+                         "single-snapshot field (same generator and parameters), times the "
+                         "distinct walks done, over the batched time"),
+        "rows_accounting": None if per_receiver_bytes is None else {
+            "frac": per_receiver_bytes * total / (rx["batched_ms"] * 1e-3) / 1e9 / hbm_peak,
+            "note": "every row counted as its own walk, although only the distinct ones are "
+                    "walked and the rest are copied: not a memory roofline"},
+        "bucket": {
+            "flags": "TREVR2_BUCKET (per-bucket beams, the paper's scheme; the plain arm is "
+                     "trevr2_J with TREVR2_BUCKET per subset)",
+            "distinct_buckets": int(buckets), "plain_bucket_walks": int(plain_bucket_walks),
+            **bk,
+            "batched_units_per_s": units / (bk["batched_ms"] * 1e-3),
+            "plain_units_per_s": units / (bk["plain_ms"] * 1e-3),
+            "roofline": roof(None if per_bucket_walk_bytes is None else
+                             per_bucket_walk_bytes * buckets + per_receiver_eval_bytes * distinct,
+                             bk["batched_ms"],
+                             "distinct (snapshot, bucket) walks + distinct receivers evaluated",
+                             "algorithmic bytes of a bucket walk from the oracle's per-bucket "
+                             "counts, plus per receiver one source record per source and its J "
+                             "row"),
+        },
     }
-    plan.free()
     for tr in trees:
         tr.free()
     return out

@@ -134,9 +134,10 @@ int trevr2_build(const double* pos, const float* mass, const float* kappa, const
  *          built per nside and averaging on first use ([nodes][N_ray] per
  *          band and length); an accepted cell's source then takes the beam
  *          only up to its projected edge s - d and adds its own ray towards
- *          the bucket.  trevr2_J_backward, the batches and trevr2_J_noalloc
- *          take none of TREVR2_BUCKET, TREVR2_PP, TREVR2_CSM (EUNSUPPORTED,
- *          EUNSUPPORTED, EINVAL).
+ *          the bucket.  Batch plans take TREVR2_BUCKET with or without
+ *          TREVR2_PP and TREVR2_CSM.  trevr2_J_backward returns EUNSUPPORTED
+ *          for any of the three and trevr2_J_noalloc EINVAL (an unknown flag
+ *          bit there).
  *  J       [A][nbsel] float32 output, overwritten
  * Active indices outside [0, N) give EINVAL (their rows are set to NaN).
  * Without TREVR2_ASYNC the call synchronises `stream` and returns any device
@@ -259,7 +260,11 @@ int trevr2_J_backward(trevr2_tree* tree, const int64_t* active, int64_t A, int n
  * bit.  Rows asking for the same receiver of the same tree (in one subset or
  * in several) are walked once and copied: a run sorts the rows by (tree,
  * receiver position in the tree's Morton order), walks the distinct ones in
- * that order and scatters the results.
+ * that order and scatters the results.  With TREVR2_BUCKET (the paper's own
+ * per-bucket beams, Sec. 2.5.1; optionally with TREVR2_PP and TREVR2_CSM) a
+ * run walks every distinct (tree, bucket) once, from the bucket centre, for
+ * all the distinct receivers of that bucket that any subset asks for: each
+ * row still equals trevr2_J's row for the same tree, receiver and flags.
  */
 typedef struct trevr2_batch trevr2_batch;
 
@@ -273,7 +278,11 @@ typedef struct trevr2_batch trevr2_batch;
  *           plan and must not be rebuilt while it exists
  *  offsets  host [nsub + 1] int64, offsets[0] = 0, non-decreasing
  *  tree_of  host [nsub] int, tree index of each subset
- *  nside, theta, flags   as for trevr2_J (TREVR2_ASYNC is ignored here)
+ *  nside, theta, flags   as for trevr2_J (TREVR2_ASYNC is ignored here);
+ *           TREVR2_PP and TREVR2_CSM need TREVR2_BUCKET (else EINVAL).  A
+ *           plan with TREVR2_PP holds the p-p particle arrays of every
+ *           resident warp (about 208 KiB each); with TREVR2_CSM creation
+ *           builds the trees' complex-source tables for `nside`
  *  out      receives the plan.  Creation builds any missing alpha tables of
  *           the trees for `nside`, copies offsets/tree_of to the device and
  *           allocates the walk buffers of the default launch shape and the
@@ -301,8 +310,9 @@ int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const int64_t* of
 int trevr2_batch_run(trevr2_batch* batch, const int64_t* active, float* J, void* stream);
 
 /*
- * trevr2_batch_autotune — times every launch shape (4 or 8 warps per block
- * x 512, 1024 or 2048 staged sources per warp and pass) on the first
+ * trevr2_batch_autotune — times every launch shape (4 or 8 warps per block,
+ * 4 only with TREVR2_BUCKET, x 512, 1024 or 2048 staged sources per warp
+ * and pass) on the first
  * min(offsets[nsub], 65536) rows of `active`, keeps the fastest for later
  * runs and re-sizes the buffers for it.  `J` is overwritten (its first rows).
  * warps_out / staging_out (host, may be NULL) receive the chosen shape.

@@ -747,6 +747,19 @@ struct BatchArgs {
   int npix;
   int max_depth;
   unsigned long long* counter;
+  // per-bucket plans (TREVR2_BUCKET): for each distinct key, its sorted
+  // element index, its (tree, leaf) and its own row of Ju
+  uint64_t* usi;                  // [total]
+  uint64_t* ubkey;                // [total] tree << 32 | leaf (invalid: ntrees << 32)
+  int* uorder;                    // [total] identity
+};
+
+// Per-tree arguments of a per-bucket plan: the bucket walk's own arguments
+// and the topology that finds each receiver's leaf.
+struct BucketBatchArgs {
+  BucketArgs tree[kMaxBatchTrees];
+  const int* child[kMaxBatchTrees];
+  const int* first[kMaxBatchTrees];
 };
 
 // Key of every row: its tree and the receiver's position in that tree's
@@ -825,6 +838,76 @@ __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk_ba
     const int si = int(key & ((uint64_t(1) << B.key_shift) - 1));
     walk_receiver_si<NBP>(B.tree[t], si, B.Ju + int64_t(u) * B.nbsel, lane, stk, off, next_beam,
                           lstk, U, Up, V, T);
+  }
+}
+
+// Per-bucket plans: the leaf of every distinct (tree, receiver) key, down the
+// tree by the first element of each upper half.  Distinct keys are sorted by
+// (tree, element position), so a bucket's receivers are adjacent.
+__global__ void k_batch_leaf(const __grid_constant__ BatchArgs B,
+                             const __grid_constant__ BucketBatchArgs bb) {
+  const int64_t u = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (u >= int64_t(*B.n_distinct)) return;
+  const uint64_t key = B.ukeys[u];
+  const int t = int(key >> B.key_shift);
+  B.uorder[u] = int(u);
+  if (t >= B.ntrees) {
+    B.ubkey[u] = uint64_t(B.ntrees) << 32;
+    B.usi[u] = 0;
+    return;
+  }
+  const int si = int(key & ((uint64_t(1) << B.key_shift) - 1));
+  const int* child = bb.child[t];
+  const int* first = bb.first[t];
+  int q = 0;
+  for (int c = child[0]; c >= 0; c = child[q]) q = si < first[c + 1] ? c : c + 1;
+  B.ubkey[u] = (uint64_t(t) << 32) | uint64_t(uint32_t(q));
+  B.usi[u] = uint64_t(si);
+}
+
+// One warp per bucket of distinct keys (the paper's per-bucket walk over
+// many subsets and snapshots); slots from a global counter, a bucket walked
+// by the warp that takes its first slot.
+template <int NBP, int WARPS, bool kPP, bool kCSM>
+__global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS)
+    k_walk_bucket_batched(const __grid_constant__ BatchArgs B,
+                          const __grid_constant__ BucketBatchArgs bb) {
+  extern __shared__ int smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;
+  int* wsm = smem + wib * (B.stack_ints + 2 * B.npix + 36 + 8 * (B.max_depth + 1));
+  int* stk = wsm;
+  int* off = wsm + B.stack_ints;
+  int* next_beam = off + 2 * B.npix + 32;
+  int* lstk = stk + lane * (B.max_depth + 2);
+  SrcEntry* U = B.srcU + gw * B.M;
+  int* Up = B.pixU + gw * B.M;
+  SrcEntry* V = B.srcV + gw * B.M;
+  float* T = B.srcT + gw * B.M * 4;
+  const int64_t nd = *B.n_distinct;
+  for (;;) {
+    unsigned long long slot = 0;
+    if (lane == 0) slot = atomicAdd(B.counter, 1ull);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (slot >= (unsigned long long)nd) break;
+    const int64_t p0 = int64_t(slot);
+    const uint64_t bkey = B.ubkey[p0];
+    const int t = int(bkey >> 32);
+    if (t >= B.ntrees) break;  // invalid receivers sort last
+    if (p0 > 0 && B.ubkey[p0 - 1] == bkey) continue;  // not the first slot of its bucket
+    int64_t p1 = p0 + 1;
+    for (;;) {
+      const int64_t p = p1 + lane;
+      const unsigned same = __ballot_sync(0xffffffffu, p < nd && B.ubkey[p] == bkey);
+      if (same == 0xffffffffu) {
+        p1 += 32;
+        continue;
+      }
+      p1 += __ffs(~same) - 1;
+      break;
+    }
+    walk_bucket<NBP, kPP, kCSM>(B.tree[t], bb.tree[t], p0, p1, int(uint32_t(bkey)), gw, lane, stk,
+                                off, next_beam, lstk, U, Up, V, T);
   }
 }
 
@@ -1130,6 +1213,21 @@ static const void* bucket_kernel_nbp(bool pp, bool csm) {
 // sphere holds more is reported (EUNSUPPORTED).
 constexpr int kPPCapacity = 4096;
 
+template <int NBP>
+static const void* bucket_batched_kernel_nbp(bool pp, bool csm) {
+  if (csm)
+    return pp ? reinterpret_cast<const void*>(&k_walk_bucket_batched<NBP, kWalkWarps, true, true>)
+              : reinterpret_cast<const void*>(&k_walk_bucket_batched<NBP, kWalkWarps, false, true>);
+  return pp ? reinterpret_cast<const void*>(&k_walk_bucket_batched<NBP, kWalkWarps, true, false>)
+            : reinterpret_cast<const void*>(&k_walk_bucket_batched<NBP, kWalkWarps, false, false>);
+}
+
+static const void* bucket_batched_kernel(int nbp, bool pp, bool csm) {
+  return nbp == 1 ? bucket_batched_kernel_nbp<1>(pp, csm)
+       : nbp == 2 ? bucket_batched_kernel_nbp<2>(pp, csm)
+                  : bucket_batched_kernel_nbp<4>(pp, csm);
+}
+
 // TREVR2_BUCKET: receivers in Morton order, the leaf of each, one warp per
 // bucket.
 static int launch_walk_bucket(Tree* t, Table* tb, const int64_t* active, int64_t A, int nside,
@@ -1363,13 +1461,18 @@ struct Batch {
   size_t smem = 0;
   int64_t blocks = 0;
   cudaStream_t last_stream = nullptr;
+  // per-bucket plans (TREVR2_BUCKET, with TREVR2_PP / TREVR2_CSM)
+  bool bucket = false;
+  bool pp = false;
+  bool csm = false;
+  BucketBatchArgs bb;
   BatchArgs args;
 };
 
 // Grid and buffers of a batch launch for (warps, M); grows the buffers.
 static int batch_shape(Batch* b, int warps, int M, int64_t limit, const void** fn, size_t* smem,
                        int64_t* blocks, cudaStream_t st) {
-  *fn = walk_kernel(b->nbp, warps, true);
+  *fn = b->bucket ? bucket_batched_kernel(b->nbp, b->pp, b->csm) : walk_kernel(b->nbp, warps, true);
   *smem = walk_smem(warps, b->args.stack_ints, b->args.npix, b->args.max_depth);
   int per_sm = 0, sms = 0;
   T2_CHECK(config_walk_kernel(*fn, warps, *smem, &per_sm, &sms));
@@ -1377,7 +1480,12 @@ static int batch_shape(Batch* b, int warps, int M, int64_t limit, const void** f
   g = std::min<int64_t>(g, (limit + warps - 1) / warps);
   *blocks = std::max<int64_t>(g, 1);
   const size_t nw = size_t(*blocks) * warps;
-  const size_t need = walk_buffer_bytes(nw, M);
+  // per-bucket plans: the warps' FP64 origin slots and p-p particle arrays
+  const size_t wb = (walk_buffer_bytes(nw, M) + 255) & ~size_t(255);
+  const size_t ob = b->bucket ? (nw * kOriginWords * sizeof(double) + 255) & ~size_t(255) : 0;
+  const size_t pp_cap = b->pp ? kPPCapacity : 0;
+  const size_t pb = nw * pp_cap * (3 * sizeof(float4) + sizeof(int));
+  const size_t need = wb + ob + pb;
   if (b->scratch_bytes < need) {
     if (b->scratch) cudaFreeAsync(b->scratch, st);
     b->scratch = nullptr;
@@ -1390,6 +1498,20 @@ static int batch_shape(Batch* b, int warps, int M, int64_t limit, const void** f
                      &b->args.srcT, &b->args.pixU);
   b->args.M = M;
   for (size_t i = 0; i < b->trees.size(); ++i) b->args.tree[i].M = M;
+  if (b->bucket) {
+    char* base = static_cast<char*>(b->scratch);
+    double* origin = reinterpret_cast<double*>(base + wb);
+    float4* pp = reinterpret_cast<float4*>(base + wb + ob);
+    for (size_t i = 0; i < b->trees.size(); ++i) {
+      b->args.tree[i].origin64 = origin;
+      BucketArgs& bk = b->bb.tree[i];
+      bk.pp_cap = int(pp_cap);
+      bk.pp_xh = b->pp ? pp : nullptr;
+      bk.pp_kc = b->pp ? pp + nw * pp_cap : nullptr;
+      bk.pp_w = b->pp ? pp + 2 * nw * pp_cap : nullptr;
+      bk.pp_si = b->pp ? reinterpret_cast<int*>(pp + 3 * nw * pp_cap) : nullptr;
+    }
+  }
   return TREVR2_OK;
 }
 
@@ -1417,8 +1539,17 @@ static int batch_enqueue(Batch* b, const int64_t* active, float* J, cudaStream_t
   k_batch_first<<<g, 256, 0, st>>>(b->args); note_launch();
   T2_CHECK(scan_exclusive_i32(b->args.first_scan, R, b->args.n_distinct, st, b->scan_ws));
   k_batch_distinct<<<g, 256, 0, st>>>(b->args); note_launch();
-  void* argv[] = {&b->args};
-  T2_CUDA(cudaLaunchKernel(b->fn, dim3(unsigned(b->blocks)), dim3(b->warps * 32), argv, b->smem, st));
+  if (b->bucket) {
+    k_batch_leaf<<<g, 256, 0, st>>>(b->args, b->bb);
+    note_launch();
+    void* argv[] = {&b->args, &b->bb};
+    T2_CUDA(cudaLaunchKernel(b->fn, dim3(unsigned(b->blocks)), dim3(b->warps * 32), argv, b->smem,
+                             st));
+  } else {
+    void* argv[] = {&b->args};
+    T2_CUDA(cudaLaunchKernel(b->fn, dim3(unsigned(b->blocks)), dim3(b->warps * 32), argv, b->smem,
+                             st));
+  }
   note_launch();
   k_batch_scatter<<<g, 256, 0, st>>>(b->args); note_launch();
   T2_CUDA(cudaGetLastError());
@@ -1459,13 +1590,15 @@ extern "C" int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const 
               TREVR2_MAX_NSIDE);
     return nside > TREVR2_MAX_NSIDE ? TREVR2_EUNSUPPORTED : TREVR2_EINVAL;
   }
-  if (flags & (TREVR2_BUCKET | TREVR2_PP | TREVR2_CSM)) {
-    set_error("trevr2_batch_create: TREVR2_BUCKET, TREVR2_PP and TREVR2_CSM are trevr2_J "
-              "flags only");
-    return TREVR2_EUNSUPPORTED;
+  if (!(theta > 0.0f) || !std::isfinite(theta) ||
+      (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_ASYNC | TREVR2_BUCKET |
+                 TREVR2_PP | TREVR2_CSM))) {
+    set_error("trevr2_batch_create: theta must be positive and finite, flags "
+              "SOFT|THICK|LINEAR|BUCKET|PP|CSM|ASYNC");
+    return TREVR2_EINVAL;
   }
-  if (!(theta > 0.0f) || !std::isfinite(theta) || (flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_LINEAR | TREVR2_ASYNC))) {
-    set_error("trevr2_batch_create: theta must be positive and finite, flags SOFT|THICK|ASYNC");
+  if ((flags & (TREVR2_PP | TREVR2_CSM)) && !(flags & TREVR2_BUCKET)) {
+    set_error("trevr2_batch_create: TREVR2_PP and TREVR2_CSM need TREVR2_BUCKET");
     return TREVR2_EINVAL;
   }
   const int nb = reinterpret_cast<Tree*>(trees[0])->nb;
@@ -1508,7 +1641,11 @@ extern "C" int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const 
   b->total = nsub > 0 ? offsets[nsub] : 0;
   b->nbp = nbp_of(nb);
   b->last_stream = st;
+  b->bucket = (flags & TREVR2_BUCKET) != 0;
+  b->pp = (flags & TREVR2_PP) != 0;
+  b->csm = (flags & TREVR2_CSM) != 0;
   std::memset(&b->args, 0, sizeof(BatchArgs));
+  std::memset(&b->bb, 0, sizeof(BucketBatchArgs));
   int max_depth = 0;
   int bsel[TREVR2_MAX_BANDS];
   for (int k = 0; k < nb; ++k) bsel[k] = k;
@@ -1520,7 +1657,31 @@ extern "C" int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const 
     Table* tb = nullptr;
     int rc = ensure_table(t, nside, st, &tb, (flags & TREVR2_LINEAR) != 0);
     if (rc) return fail(rc);
-    fill_walk_args(t, tb, nside, theta, bsel, nb, flags & ~TREVR2_ASYNC, kSrcCapacity, &b->args.tree[i]);
+    if (!b->bucket) {
+      fill_walk_args(t, tb, nside, theta, bsel, nb, flags & ~TREVR2_ASYNC, kSrcCapacity,
+                     &b->args.tree[i]);
+      continue;
+    }
+    // the walk from the bucket centre takes no receiver flags; they go to the
+    // bucket arguments (as in trevr2_J with TREVR2_BUCKET)
+    WalkArgs& a = b->args.tree[i];
+    fill_walk_args(t, tb, nside, theta, bsel, nb,
+                   flags & ~(TREVR2_SOFT | TREVR2_THICK | TREVR2_ASYNC), kSrcCapacity, &a);
+    if (b->csm) {
+      rc = ensure_csm(t, tb, st);
+      if (rc) return fail(rc);
+      a.csm_tau = tb->csm_tau;
+      a.csm_d = tb->csm_d;
+      a.csm_anti = tb->csm_anti;
+    }
+    BucketArgs& bk = b->bb.tree[i];
+    bk.rflags = flags & (TREVR2_SOFT | TREVR2_THICK);
+    bk.pp = b->pp ? 1 : 0;
+    bk.beam = std::sqrt(4.0 * M_PI / double(12 * nside * nside));
+    bk.mass = t->mass;
+    bk.directed = 0;
+    b->bb.child[i] = t->child;
+    b->bb.first[i] = t->first;
   }
   // one shared-memory layout for all trees: the deepest one's
   for (int i = 0; i < ntrees; ++i) {
@@ -1549,7 +1710,8 @@ extern "C" int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const 
     const size_t R = size_t(b->total);
     const size_t bk = up(8 * R), br = up(4 * R), bu = up(4 * R * nb);
     const size_t bsort = up(radix_ws_bytes(int64_t(R))), bscan = up(4 * scan_ws_ints(int64_t(R)));
-    const size_t bytes = bk * 2 + br * 2 + bu + 256 + bsort + bscan;
+    const size_t bbuck = b->bucket ? bk * 2 + br : 0;  // usi, ubkey, uorder
+    const size_t bytes = bk * 2 + br * 2 + bu + 256 + bsort + bscan + bbuck;
     cudaError_t e = cudaMallocAsync(&b->dedup, bytes, st);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMallocAsync(batch deduplication)"));
     char* p = static_cast<char*>(b->dedup);
@@ -1560,7 +1722,19 @@ extern "C" int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const 
     b->args.Ju = reinterpret_cast<float*>(p); p += bu;
     b->args.n_distinct = reinterpret_cast<int*>(p); p += 256;
     b->sort_ws = p; p += bsort;
-    b->scan_ws = reinterpret_cast<int*>(p);
+    b->scan_ws = reinterpret_cast<int*>(p); p += bscan;
+    if (b->bucket) {
+      b->args.usi = reinterpret_cast<uint64_t*>(p); p += bk;
+      b->args.ubkey = reinterpret_cast<uint64_t*>(p); p += bk;
+      b->args.uorder = reinterpret_cast<int*>(p);
+      // the per-bucket walk writes each distinct key's row of Ju through its
+      // order (the identity)
+      for (int i = 0; i < ntrees; ++i) {
+        b->args.tree[i].J = b->args.Ju;
+        b->args.tree[i].order = b->args.uorder;
+        b->bb.tree[i].keys = b->args.usi;
+      }
+    }
   }
   if (nsub > 0) {
     cudaError_t e = cudaMemcpyAsync(b->d_offsets, offsets, (size_t(nsub) + 1) * sizeof(int64_t),
@@ -1615,15 +1789,18 @@ extern "C" int trevr2_batch_autotune(trevr2_batch* batch, const int64_t* active,
     // time each (warps per block, source staging depth) on a prefix of the
     // work and keep the fastest
     const int64_t limit = std::min<int64_t>(b->total, 65536);
+    // the per-bucket walk is compiled for one block shape
     const int cand_w[2] = {4, 8};
+    const int n_w = b->bucket ? 1 : 2;
     const int cand_m[3] = {512, 1024, 2048};
     cudaEvent_t e0, e1;
     T2_CUDA(cudaEventCreate(&e0));
     T2_CUDA(cudaEventCreate(&e1));
     float best = INFINITY;
     int bw = b->warps, bm = b->M;
-    for (int w : cand_w)
+    for (int iw = 0; iw < n_w; ++iw)
       for (int m : cand_m) {
+        const int w = cand_w[iw];
         int rc = batch_select(b, w, m, limit, st);
         if (!rc) rc = batch_enqueue(b, active, J, st);  // warm-up
         if (!rc) {

@@ -111,6 +111,90 @@ def test_batch_equals_per_subset_and_oracle(t2, oracle_mod, nside, flags):
         tr.free()
 
 
+@pytest.mark.parametrize("nside,extra", [(2, 0), (1, 3), (2, 34), (2, 64), (4, 96 + 2)])
+def test_batch_bucket_equals_per_subset_and_oracle(t2, oracle_mod, nside, extra):
+    """Per-bucket plans (TREVR2_BUCKET, Sec. 2.5.1; with SOFT|THICK, with p-p
+    absorption and THICK, with the complex source model, with both): every
+    distinct (tree, bucket) is walked once for all the receivers the
+    subsets ask for, and each subset's rows equal trevr2_J's per-bucket rows
+    for that subset bit for bit and the oracle within the J tolerances."""
+    flags = t2.BUCKET | extra
+    cases = _small_cases()
+    trees = [_gpu_tree(t2, c) for c in cases]
+    subs = _subsets(cases, seed=21)
+    active, offsets, tree_of = _layout(subs)
+    J = t2.J_batched(trees, active, offsets, tree_of, nside, 0.75, flags).cpu().numpy()
+    oracles = [oracle_mod.OracleTree.from_case(c) for c in cases]
+    for s, (t, m) in enumerate(subs):
+        rows = J[offsets[s]:offsets[s + 1]]
+        if len(m) == 0:
+            continue
+        single = trees[t].J(m, nside, 0.75, flags=flags).cpu().numpy()
+        np.testing.assert_array_equal(rows, single, err_msg=f"subset {s} (tree {t})")
+        _assert_J(rows, oracles[t].J(m, nside, 0.75, flags=flags), f"subset {s}")
+    for tr in trees:
+        tr.free()
+
+
+def test_batch_bucket_graph_replay_and_autotune(t2, oracle_mod):
+    """A per-bucket plan autotuned, recorded into a CUDA graph and replayed
+    with other receivers in the same buffer."""
+    cases = _small_cases()
+    trees = [_gpu_tree(t2, c) for c in cases]
+    subs = _subsets(cases, seed=22)
+    active, offsets, tree_of = _layout(subs)
+    plan = t2.Batch(trees, offsets, tree_of, nside=2, theta=0.6, flags=t2.BUCKET)
+    act = torch.as_tensor(active, device="cuda")
+    w, m = plan.autotune(act)
+    assert w == 4 and m in (512, 1024, 2048)
+    out = torch.empty((int(offsets[-1]), 2), dtype=torch.float32, device="cuda")
+    plan.run(act, out)
+    plan.status()
+    ref = out.cpu().numpy().copy()
+    for s, (t, mem) in enumerate(subs):
+        if len(mem):
+            want = oracle_mod.OracleTree.from_case(cases[t]).J(mem, 2, 0.6, flags=t2.BUCKET)
+            _assert_J(ref[offsets[s]:offsets[s + 1]], want, f"autotuned bucket subset {s}")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.run(act, out)
+    out.fill_(-1.0)
+    g.replay()
+    torch.cuda.synchronize()
+    plan.status()
+    np.testing.assert_array_equal(out.cpu().numpy(), ref)
+    rng = np.random.default_rng(4)
+    perm = np.arange(len(active))
+    for s in range(len(subs)):
+        lo, hi = offsets[s], offsets[s + 1]
+        perm[lo:hi] = lo + rng.permutation(hi - lo)
+    act.copy_(torch.as_tensor(active[perm], device="cuda"))
+    g.replay()
+    torch.cuda.synchronize()
+    plan.status()
+    np.testing.assert_array_equal(out.cpu().numpy(), ref[perm])
+    plan.free()
+    for tr in trees:
+        tr.free()
+
+
+def test_batch_bucket_bad_receiver_reported(t2):
+    cases = _small_cases()[:2]
+    trees = [_gpu_tree(t2, c) for c in cases]
+    n0 = len(cases[0]["pos"])
+    subs = [(0, np.array([0, n0, 1], np.int64)), (1, np.array([5, 6], np.int64))]
+    active, offsets, tree_of = _layout(subs)
+    plan = t2.Batch(trees, offsets, tree_of, nside=2, flags=t2.BUCKET)
+    J = plan.run(torch.as_tensor(active, device="cuda"))
+    with pytest.raises(t2.TrevrError, match="EINVAL"):
+        plan.status()
+    J = J.cpu().numpy()
+    assert np.all(np.isnan(J[1])) and np.all(np.isfinite(J[[0, 2, 3, 4]]))
+    plan.free()
+    for tr in trees:
+        tr.free()
+
+
 def test_batch_plan_reuse_and_graph_replay(t2, oracle_mod):
     """One plan run eagerly, then recorded into a CUDA graph and replayed with
     new receivers written into the same input buffer."""
@@ -241,15 +325,17 @@ def snapshots():
     return workloads.batched_cases()
 
 
-def test_batch_full_size_sampled(t2, oracle_mod, snapshots):
+@pytest.mark.parametrize("flags", [0, 16])
+def test_batch_full_size_sampled(t2, oracle_mod, snapshots, flags):
     """The individual-timestep workload at full size: 4 snapshots of the
     2,097,152-element clumpy 3-band field, 64 subsets each of 10^U(2,6)
-    receivers, nside 4, theta 0.5, autotuned, one launch; 512 sampled rows
-    against the oracle."""
+    receivers, nside 4, theta 0.5, autotuned, one launch (per receiver, and
+    per bucket with TREVR2_BUCKET = 16); 512 sampled rows against the
+    oracle."""
     snaps, subsets = snapshots
     trees = [_gpu_tree(t2, c) for c in snaps]
     active, offsets, tree_of = _layout(subsets)
-    plan = t2.Batch(trees, offsets, tree_of, nside=4, theta=0.5)
+    plan = t2.Batch(trees, offsets, tree_of, nside=4, theta=0.5, flags=flags)
     act = torch.as_tensor(active, device="cuda")
     plan.autotune(act)
     J = plan.run(act).cpu().numpy()
@@ -261,7 +347,7 @@ def test_batch_full_size_sampled(t2, oracle_mod, snapshots):
     for t in range(len(snaps)):
         pick = rows[tree_of[sub_of_row] == t]
         if len(pick):
-            ref = oracle_mod.OracleTree.from_case(snaps[t]).J(active[pick], 4, 0.5)
+            ref = oracle_mod.OracleTree.from_case(snaps[t]).J(active[pick], 4, 0.5, flags=flags)
             _assert_J(J[pick], ref, f"snapshot {t}")
     plan.free()
     for tr in trees:

@@ -129,8 +129,11 @@ def test_bucket_bad_receiver_and_unsupported_calls(t2):
     with pytest.raises(t2.TrevrError, match="EUNSUPPORTED"):
         tree.J_backward(case["active"][:10], np.ones((10, 2), np.float32), 2, 0.75,
                         flags=BUCKET)
-    with pytest.raises(t2.TrevrError, match="EUNSUPPORTED"):
-        t2.Batch([tree], [0, 5], [0], flags=BUCKET)
+    # batch plans take BUCKET (tests/test_gpu_batch.py); PP and CSM need it
+    with pytest.raises(t2.TrevrError, match="EINVAL"):
+        t2.Batch([tree], [0, 5], [0], flags=t2.PP)
+    with pytest.raises(t2.TrevrError, match="EINVAL"):
+        t2.Batch([tree], [0, 5], [0], flags=t2.CSM)
     assert tree.J(np.zeros(0, np.int64), 2, 0.75, flags=BUCKET).shape == (0, 2)
     tree.free()
 
