@@ -41,7 +41,8 @@ extern "C" {
 #define TREVR2_EINVAL (-1)      /* invalid argument or input value            */
 #define TREVR2_ENOMEM (-2)      /* device or host allocation failed           */
 #define TREVR2_ECUDA (-3)       /* a CUDA runtime call failed                 */
-#define TREVR2_ETIMEOUT (-4)    /* a bounded device wait gave up              */
+#define TREVR2_ETIMEOUT (-4)    /* reserved: no kernel of this library waits on
+                                   the device, so no call returns it           */
 #define TREVR2_EUNSUPPORTED (-5)/* outside the supported sizes (see below)    */
 #define TREVR2_EINTERNAL (-6)   /* an internal capacity check failed          */
 
@@ -213,9 +214,11 @@ int trevr2_prepare(trevr2_tree* tree, int nside, void* stream);
  * Every process that loads the library holds that array on each GPU it uses
  * until it exits.  All calls share the array: calls whose work overlaps on
  * the GPU (on any tree, from any thread or stream) race and must be ordered
- * by the caller.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.
+ * by the caller.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress) with the tree's device current, so the address
+ * stays right if the device's context is reset; the first call on a device
+ * also loads the library's module there, so make that first call before any
+ * stream capture.
  */
 int trevr2_J_noalloc(trevr2_tree* tree, const int64_t* active, int64_t A, int nside, float theta,
                      const int* bands, int nbsel, uint32_t flags, float* J, void* stream);
@@ -345,6 +348,36 @@ int trevr2_free(trevr2_tree* tree);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char* trevr2_last_error(void);
+
+/* ---- Testing aids ---------------------------------------------------
+ * These make a later call fail on the host side, so that the error paths of
+ * the library can be tested without faulting a GPU.  Process wide, for tests
+ * only; both are off by default.
+ */
+#define TREVR2_DEBUG_FAIL_ALLOC 1   /* value n >= 0: the (n+1)-th device allocation
+                                       of the library from now on fails with
+                                       ENOMEM (then the setting is off again);
+                                       -1 turns it off */
+#define TREVR2_DEBUG_SOURCE_STACK 2 /* value c > 0: the warp-wide stack of the
+                                       source cut (Sec. 2.5.2) holds at most c
+                                       entries, so that a deep cut overflows it
+                                       and the walk reports EINTERNAL; 0 restores
+                                       the full capacity.  Read when a walk is
+                                       set up (trevr2_J, trevr2_J_backward,
+                                       trevr2_batch_create) */
+
+/* Sets one testing aid (EINVAL for an unknown `what` or a value out of range). */
+int trevr2_debug_set(int what, int64_t value);
+
+/* Bytes the library currently holds in the current device's default
+ * stream-ordered memory pool, which only this library allocates from
+ * (synchronises the device first; ECUDA if the query fails). */
+int trevr2_debug_pool_used(uint64_t* bytes);
+
+/* The architecture the library's kernels run as on the current device
+ * (major * 10 + minor of the loaded binary, from the walk kernel's
+ * attributes; 103 for sm_103a).  ECUDA without a usable device. */
+int trevr2_kernel_binary_version(int* version);
 
 /* Number of CUDA kernels this library has launched in this process so far
  * (a host-side count of launch calls, for accounting in benchmarks). */

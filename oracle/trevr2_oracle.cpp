@@ -20,8 +20,8 @@
 //
 // Readings of the paper that this file fixes (each is also listed in the
 // design notes):
-//  R1 Tree: "half-way along the longest axis" of a cube is cyclic x,y,z
-//     bisection (ties x<y<z), i.e. the bisection of 63-bit Morton keys
+//  R1 Tree: splitting each cell at the middle of its longest side, from a
+//     cube root, is cyclic x,y,z bisection (ties x<y<z), i.e. the bisection of 63-bit Morton keys
 //     (21 bits per axis, bit 62 = x MSB).  Cells are the geometric bisection
 //     boxes, not tight particle bounds.  A node splits iff it holds more than
 //     `bucket` elements and depth < 63; empty halves are empty leaves.

@@ -32,7 +32,8 @@ import torch
 __all__ = [
     "SOFT", "THICK", "ASYNC", "Tree", "TrevrError", "build", "J", "library_path", "load_library",
     "healpix_pix2vec", "healpix_vec2pix", "exported_symbols", "FIELDS", "kernel_launches",
-    "Batch", "J_batched", "J_fn", "LINEAR", "BUCKET", "PP", "CSM",
+    "Batch", "J_batched", "J_fn", "LINEAR", "BUCKET", "PP", "CSM", "debug_set",
+    "debug_pool_used", "DEBUG_FAIL_ALLOC", "DEBUG_SOURCE_STACK",
 ]
 
 SOFT = 1
@@ -82,6 +83,31 @@ class _Info(C.Structure):
 def kernel_launches() -> int:
     """Kernels launched by libtrevr2 in this process so far."""
     return int(load_library().trevr2_kernel_launches())
+
+
+def kernel_binary_version() -> int:
+    """Architecture of the loaded kernels on the current device (103 = sm_103a)."""
+    v = C.c_int(0)
+    _check(load_library().trevr2_kernel_binary_version(C.byref(v)))
+    return int(v.value)
+
+
+DEBUG_FAIL_ALLOC = 1
+DEBUG_SOURCE_STACK = 2
+
+
+def debug_set(what: int, value: int) -> None:
+    """Testing aid: DEBUG_FAIL_ALLOC (the n-th device allocation from now on
+    fails with ENOMEM; -1 turns it off) or DEBUG_SOURCE_STACK (cap the source
+    cut's stack at c entries; 0 restores it)."""
+    _check(load_library().trevr2_debug_set(int(what), int(value)))
+
+
+def debug_pool_used() -> int:
+    """Bytes libtrevr2 holds in the current device's default memory pool."""
+    v = C.c_uint64(0)
+    _check(load_library().trevr2_debug_pool_used(C.byref(v)))
+    return int(v.value)
 
 
 def library_path() -> str:
@@ -135,6 +161,9 @@ def load_library():
                 fn.restype = C.c_int
         lib.trevr2_kernel_launches.restype = C.c_uint64
         lib.trevr2_kernel_launches.argtypes = []
+        lib.trevr2_debug_set.argtypes = [i32, i64]
+        lib.trevr2_kernel_binary_version.argtypes = [C.POINTER(C.c_int)]
+        lib.trevr2_debug_pool_used.argtypes = [C.POINTER(C.c_uint64)]
         _lib = lib
         return lib
 

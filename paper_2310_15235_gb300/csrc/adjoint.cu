@@ -442,7 +442,7 @@ __device__ __forceinline__ void adjoint_receiver(const AdjArgs& g, int64_t slot,
 #pragma unroll
   for (int b = 0; b < NBP; ++b) Js[b] = Jc[b] = 0.0f;
   for (int lo = 0;; lo += a.M) {
-    const int total = phase_sources(a, x, si, lane, stk, a.stack_ints, U, Up, lo);
+    const int total = phase_sources(a, x, si, lane, stk, a.src_stack_cap, U, Up, lo);
     const int staged = min(total - lo, a.M);
     make_sources(a, x, si, lane, U, Up, staged);
     const int n = staged > 0 ? bin_sources(a, lane, U, Up, staged, V, off) : 0;
@@ -721,11 +721,8 @@ extern "C" int trevr2_J_backward(trevr2_tree* tree, const int64_t* active, int64
   const size_t b_seg = up(sizeof(float4) * warps * size_t(seg_cap) * 32);
   const size_t b_walk = warps * size_t(wa.M) * (2 * sizeof(SrcEntry) + sizeof(int));
   char* base = nullptr;
-  {
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base),
-                                    zeroed + b_leaf + b_T + b_Q + b_seg + b_walk, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(adjoint buffers)");
-  }
+  T2_CHECK(device_alloc(reinterpret_cast<void**>(&base),
+                        zeroed + b_leaf + b_T + b_Q + b_seg + b_walk, st, "adjoint buffers"));
   AdjArgs g;
   std::memset(&g, 0, sizeof(g));
   g.w = wa;

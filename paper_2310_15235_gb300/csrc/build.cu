@@ -40,6 +40,38 @@ int cuda_fail(cudaError_t e, const char* what) {
 }
 
 // ---------------------------------------------------------------------------
+// Device allocations, and the failures a test can ask for (testing aids).
+static std::atomic<int64_t> g_fail_alloc_after{-1};   // -1: off
+static std::atomic<int> g_source_stack_cap{0};        // 0: off
+
+// True for the one allocation a test asked to fail (then off again).
+static bool injected_alloc_failure() {
+  int64_t v = g_fail_alloc_after.load();
+  while (v >= 0)
+    if (g_fail_alloc_after.compare_exchange_weak(v, v - 1)) return v == 0;
+  return false;
+}
+
+int device_alloc(void** p, size_t bytes, cudaStream_t st, const char* what) {
+  *p = nullptr;
+  if (injected_alloc_failure()) {
+    set_error("%s of %zu bytes failed: out of memory (failure requested by "
+              "trevr2_debug_set)", what, bytes);
+    return TREVR2_ENOMEM;
+  }
+  cudaError_t e = cudaMallocAsync(p, bytes, st);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    set_error("%s of %zu bytes failed: %s", what, bytes, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? TREVR2_ENOMEM : TREVR2_ECUDA;
+  }
+  return TREVR2_OK;
+}
+
+int debug_source_stack_cap() { return g_source_stack_cap.load(); }
+
+// ---------------------------------------------------------------------------
 // Exclusive scan (block scan of 2048 values + recursive scan of block sums).
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 2 * kScanThreads;
@@ -209,10 +241,7 @@ int radix_sort_u64_i32(uint64_t* keys, int* vals, int64_t n, cudaStream_t st, in
   passes += passes & 1;
   const int ntiles = int((n + kSortTile - 1) / kSortTile);
   const bool own = ws == nullptr;
-  if (own) {
-    cudaError_t e = cudaMallocAsync(&ws, radix_ws_bytes(n), st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(sort workspace)");
-  }
+  if (own) T2_CHECK(device_alloc(&ws, radix_ws_bytes(n), st, "sort workspace"));
   auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
   char* p = static_cast<char*>(ws);
   uint64_t* k2 = reinterpret_cast<uint64_t*>(p);
@@ -602,19 +631,19 @@ static int build_impl(Tree* t, const double* pos, const float* mass, const float
   // 1. validation and bounding box
   const int vthreads = 256;
   const int vblocks = int(std::min<int64_t>(std::max<int64_t>(blocks_for(N, vthreads), 1), 1024));
-  double* partial = nullptr;
-  T2_CHECK(dalloc(&partial, size_t(vblocks) * 6, st));
+  DeviceTemp<double> partial(st);
+  T2_CHECK(dalloc(&partial.p, size_t(vblocks) * 6, st));
   if (N > 0)
-    k_validate<<<vblocks, vthreads, 0, st>>>(pos, mass, kappa, lum, h, N, nb, partial, t->status); note_launch();
+    k_validate<<<vblocks, vthreads, 0, st>>>(pos, mass, kappa, lum, h, N, nb, partial.p, t->status); note_launch();
   std::vector<double> hpart(size_t(vblocks) * 6);
   uint32_t hstatus = 0;
   if (N > 0) {
-    T2_CUDA(cudaMemcpyAsync(hpart.data(), partial, hpart.size() * sizeof(double),
+    T2_CUDA(cudaMemcpyAsync(hpart.data(), partial.p, hpart.size() * sizeof(double),
                             cudaMemcpyDeviceToHost, st));
     T2_CUDA(cudaMemcpyAsync(&hstatus, t->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   }
   T2_CUDA(cudaStreamSynchronize(st));
-  dfree(partial, st);
+  dfree(partial.p, st);
   if (hstatus & kStatusBadInput) {
     set_error("trevr2_build: non-finite position, or negative/non-finite mass, kappa, lum or h");
     return TREVR2_EINVAL;
@@ -683,10 +712,11 @@ static int build_impl(Tree* t, const double* pos, const float* mass, const float
   int64_t cap = 0;
   T2_CHECK(grow(t, std::max<int64_t>(1024, 4 * (N / std::max(t->bucket, 1)) + 64), cap, st));
   k_init_root<<<1, 1, 0, st>>>(N, t->prefix, t->depth, t->first, t->count, t->child, t->parent); note_launch();
-  int* flag = nullptr;
-  int* fscan = nullptr;
-  int* mid = nullptr;
-  int* dtotal = nullptr;
+  DeviceTemp<int> flag_t(st), fscan_t(st), mid_t(st), dtotal_t(st);
+  int*& flag = flag_t.p;
+  int*& fscan = fscan_t.p;
+  int*& mid = mid_t.p;
+  int*& dtotal = dtotal_t.p;
   int64_t flag_cap = 1024;
   T2_CHECK(dalloc(&flag, flag_cap, st));
   T2_CHECK(dalloc(&fscan, flag_cap, st));
@@ -750,9 +780,11 @@ static int build_impl(Tree* t, const double* pos, const float* mass, const float
   T2_CHECK(dalloc(&t->c64, 3 * n, st));
   T2_CHECK(dalloc(&t->B64, n, st));
   T2_CHECK(dalloc(&t->alpha_leaf, n * nbp, st));
-  double* L64 = nullptr;
-  double* cs64 = nullptr;
-  uint32_t* fl = nullptr;
+  DeviceTemp<double> L64_t(st), cs64_t(st);
+  DeviceTemp<uint32_t> fl_t(st);
+  double*& L64 = L64_t.p;
+  double*& cs64 = cs64_t.p;
+  uint32_t*& fl = fl_t.p;
   T2_CHECK(dalloc(&L64, 4 * n, st));
   T2_CHECK(dalloc(&cs64, 4 * n, st));
   T2_CHECK(dalloc(&fl, n, st));
@@ -780,6 +812,42 @@ using namespace trevr2;
 extern "C" {
 
 const char* trevr2_last_error(void) { return g_err; }
+
+int trevr2_debug_set(int what, int64_t value) {
+  clear_error();
+  switch (what) {
+    case TREVR2_DEBUG_FAIL_ALLOC:
+      if (value < -1) break;
+      g_fail_alloc_after.store(value);
+      return TREVR2_OK;
+    case TREVR2_DEBUG_SOURCE_STACK:
+      if (value < 0 || value > (int64_t(1) << 30)) break;
+      g_source_stack_cap.store(int(value));
+      return TREVR2_OK;
+    default:
+      break;
+  }
+  set_error("trevr2_debug_set: unknown setting %d or value %lld out of range", what,
+            static_cast<long long>(value));
+  return TREVR2_EINVAL;
+}
+
+int trevr2_debug_pool_used(uint64_t* bytes) {
+  clear_error();
+  if (!bytes) {
+    set_error("trevr2_debug_pool_used: bytes is NULL");
+    return TREVR2_EINVAL;
+  }
+  int dev = 0;
+  T2_CUDA(cudaGetDevice(&dev));
+  T2_CUDA(cudaDeviceSynchronize());
+  cudaMemPool_t pool;
+  T2_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t used = 0;
+  T2_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+  *bytes = uint64_t(used);
+  return TREVR2_OK;
+}
 
 uint64_t trevr2_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
@@ -1032,24 +1100,27 @@ extern "C" int trevr2_set_tau_refine(trevr2_tree* tree, double tau_refine, void*
   }
   const int64_t n = t->n_nodes;
   if (!t->dtau) {
-    T2_CHECK(dalloc(&t->dtau, size_t(n), st));
-    float* range = nullptr;
-    T2_CHECK(dalloc(&range, size_t(n) * 2 * t->nbp, st));
-    float* amin = range;
-    float* amax = range + size_t(n) * t->nbp;
+    // computed into temporaries and kept only when complete, so that a
+    // failed call leaves the tree as it was
+    DeviceTemp<float> dtau(st), range(st);
+    T2_CHECK(dalloc(&dtau.p, size_t(n), st));
+    T2_CHECK(dalloc(&range.p, size_t(n) * 2 * t->nbp, st));
+    float* amin = range.p;
+    float* amax = range.p + size_t(n) * t->nbp;
     for (int d = int(t->level_begin.size()) - 2; d >= 0; --d) {
       const int64_t lb = t->level_begin[d], le = t->level_begin[d + 1];
       if (le <= lb) continue;
       const unsigned g = blocks_for(le - lb, 256);
       switch (t->nbp) {
-        case 1: k_tau_variation_level<1><<<g, 256, 0, st>>>(lb, le, t->nodes, t->alpha_leaf, amin, amax, t->dtau); break;
-        case 2: k_tau_variation_level<2><<<g, 256, 0, st>>>(lb, le, t->nodes, t->alpha_leaf, amin, amax, t->dtau); break;
-        default: k_tau_variation_level<4><<<g, 256, 0, st>>>(lb, le, t->nodes, t->alpha_leaf, amin, amax, t->dtau); break;
+        case 1: k_tau_variation_level<1><<<g, 256, 0, st>>>(lb, le, t->nodes, t->alpha_leaf, amin, amax, dtau.p); break;
+        case 2: k_tau_variation_level<2><<<g, 256, 0, st>>>(lb, le, t->nodes, t->alpha_leaf, amin, amax, dtau.p); break;
+        default: k_tau_variation_level<4><<<g, 256, 0, st>>>(lb, le, t->nodes, t->alpha_leaf, amin, amax, dtau.p); break;
       }
       note_launch();
     }
     T2_CUDA(cudaGetLastError());
-    dfree(range, st);
+    t->dtau = dtau.p;
+    dtau.p = nullptr;
   }
   if (!t->nodes_refined) T2_CHECK(dalloc(&t->nodes_refined, size_t(n), st));
   k_refine_nodes<<<blocks_for(n, 256), 256, 0, st>>>(n, t->nodes, t->dtau, float(tau_refine),

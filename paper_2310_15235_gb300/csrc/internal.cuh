@@ -51,7 +51,6 @@ constexpr uint32_t kStatusBadActive = 1u << 0;
 constexpr uint32_t kStatusStackOverflow = 1u << 1;
 constexpr uint32_t kStatusBadInput = 1u << 2;
 constexpr uint32_t kStatusOutsideBox = 1u << 3;
-constexpr uint32_t kStatusTimeout = 1u << 4;
 constexpr uint32_t kStatusPPOverflow = 1u << 5;  // a p-p sphere held too many particles
 
 // Geometry of the transmission average for one cell shape and one beam pair:
@@ -155,17 +154,15 @@ void note_launch();
     if (rc_ != TREVR2_OK) return rc_; \
   } while (0)
 
+// Every device allocation of the library (stream ordered, freed with
+// dfree / cudaFreeAsync).  `what` names it in the error message.  A failure
+// requested with trevr2_debug_set(TREVR2_DEBUG_FAIL_ALLOC, n) happens here.
+int device_alloc(void** p, size_t bytes, cudaStream_t st, const char* what);
+
 template <class T>
 int dalloc(T** p, size_t count, cudaStream_t st) {
-  *p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(p), count * sizeof(T), st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    set_error("device allocation of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
-    return e == cudaErrorMemoryAllocation ? TREVR2_ENOMEM : TREVR2_ECUDA;
-  }
-  return TREVR2_OK;
+  return device_alloc(reinterpret_cast<void**>(p), count * sizeof(T), st, "device allocation");
 }
 
 template <class T>
@@ -173,6 +170,22 @@ void dfree(T*& p, cudaStream_t st) {
   if (p) cudaFreeAsync(p, st);
   p = nullptr;
 }
+
+// A temporary device buffer freed (stream ordered) when it goes out of
+// scope, so that every early error return releases it.
+template <class T>
+struct DeviceTemp {
+  T* p = nullptr;
+  cudaStream_t st;
+  explicit DeviceTemp(cudaStream_t s) : st(s) {}
+  ~DeviceTemp() { dfree(p, st); }
+  DeviceTemp(const DeviceTemp&) = delete;
+  DeviceTemp& operator=(const DeviceTemp&) = delete;
+};
+
+// Capacity of the source cut's traversal stack set by
+// trevr2_debug_set(TREVR2_DEBUG_SOURCE_STACK, c); 0 when not set.
+int debug_source_stack_cap();
 
 // Exclusive scan of n int32 values in place; *d_total (device) gets the sum.
 // ws (device, scan_ws_ints(n) ints) or NULL to allocate one stream ordered.

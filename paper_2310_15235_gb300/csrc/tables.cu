@@ -140,14 +140,23 @@ int ensure_table(Tree* t, int nside, cudaStream_t st, Table** out, bool linear) 
       *out = &tb;
       return TREVR2_OK;
     }
+  const int npix = 12 * nside * nside, P = npix / 2;
+  // built in temporaries and kept by the tree only when complete
+  DeviceTemp<float4> dirs(st);
+  DeviceTemp<double> dirs64(st);
+  DeviceTemp<TransGeo> geo(st);
+  DeviceTemp<float> alpha(st);
+  T2_CHECK(dalloc(&dirs.p, npix, st));
+  T2_CHECK(dalloc(&dirs64.p, 3 * size_t(npix), st));
+  T2_CHECK(dalloc(&geo.p, 3 * size_t(P), st));
+  T2_CHECK(dalloc(&alpha.p, size_t(std::max<int64_t>(t->n_internal, 1)) * P * t->nbp, st));
   Table tb;
   tb.nside = nside;
   tb.linear = linear;
-  const int npix = 12 * nside * nside, P = npix / 2;
-  T2_CHECK(dalloc(&tb.dirs, npix, st));
-  T2_CHECK(dalloc(&tb.dirs64, 3 * size_t(npix), st));
-  T2_CHECK(dalloc(&tb.geo, 3 * size_t(P), st));
-  T2_CHECK(dalloc(&tb.alpha, size_t(std::max<int64_t>(t->n_internal, 1)) * P * t->nbp, st));
+  tb.dirs = dirs.p;
+  tb.dirs64 = dirs64.p;
+  tb.geo = geo.p;
+  tb.alpha = alpha.p;
   k_dirs<<<(npix + 127) / 128, 128, 0, st>>>(nside, npix, tb.dirs64, tb.dirs); note_launch();
   k_trans_geo<<<(3 * P + 127) / 128, 128, 0, st>>>(P, tb.dirs64, tb.geo); note_launch();
   for (int d = t->max_depth; d >= 0; --d) {
@@ -163,6 +172,10 @@ int ensure_table(Tree* t, int nside, cudaStream_t st, Table** out, bool linear) 
   }
   T2_CUDA(cudaGetLastError());
   t->tables.push_back(tb);
+  dirs.p = nullptr;
+  dirs64.p = nullptr;
+  geo.p = nullptr;
+  alpha.p = nullptr;
   *out = &t->tables.back();
   return TREVR2_OK;
 }

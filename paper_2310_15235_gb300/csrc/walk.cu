@@ -199,7 +199,7 @@ __device__ __forceinline__ void walk_receiver_si(const WalkArgs& a, int si, floa
 #pragma unroll
   for (int b = 0; b < NBP; ++b) Js[b] = Jc[b] = 0.0f;
   for (int lo = 0;; lo += a.M) {
-    const int total = phase_sources(a, x, si, lane, stk, a.stack_ints, U, Up, lo);
+    const int total = phase_sources(a, x, si, lane, stk, a.src_stack_cap, U, Up, lo);
     const int staged = min(total - lo, a.M);
     make_sources(a, x, si, lane, U, Up, staged);
     const int n = staged > 0 ? bin_sources(a, lane, U, Up, staged, V, off) : 0;
@@ -630,7 +630,7 @@ __device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0,
 #pragma unroll
     for (int b = 0; b < NBP; ++b) acc[b] = 0.0;
     for (int lo = 0;; lo += a.M) {
-      const int total = phase_sources<true, kPP>(a, o, si_o, lane, stk, a.stack_ints, U, Up, lo,
+      const int total = phase_sources<true, kPP>(a, o, si_o, lane, stk, a.src_stack_cap, U, Up, lo,
                                                  rpp);
       const int staged = min(total - lo, a.M);
       make_sources<true, kCSM>(a, o, si_o, lane, U, Up, staged);
@@ -952,6 +952,8 @@ void fill_walk_args(const Tree* t, const Table* tb, int nside, float theta, cons
   a->M = M;
   a->max_depth = t->max_depth;
   a->stack_ints = 64 * (t->max_depth + 2);
+  a->src_stack_cap = a->stack_ints;
+  if (const int cap = debug_source_stack_cap()) a->src_stack_cap = std::min(cap, a->stack_ints);
   a->status = t->status;
   a->counter = t->counter;
 }
@@ -1004,6 +1006,18 @@ static void place_walk_buffers(char* base, size_t warps, int M, SrcEntry** U, Sr
   *Up = reinterpret_cast<int*>(base + 2 * warps * M * sizeof(SrcEntry));
 }
 
+// A grown-on-demand device buffer: at least `need` bytes in *buf.  A failed
+// allocation leaves it empty (NULL, 0 bytes), never pointing at freed memory.
+static int grow_buffer(void** buf, size_t* bytes, size_t need, cudaStream_t st, const char* what) {
+  if (*bytes >= need) return TREVR2_OK;
+  if (*buf) cudaFreeAsync(*buf, st);
+  *buf = nullptr;
+  *bytes = 0;
+  T2_CHECK(device_alloc(buf, need, st, what));
+  *bytes = need;
+  return TREVR2_OK;
+}
+
 __global__ void k_order_keys(const int64_t* __restrict__ active, int64_t A, int64_t N,
                              const int* __restrict__ inv, uint64_t* __restrict__ keys,
                              int* __restrict__ slots) {
@@ -1024,14 +1038,7 @@ static int launch_walk(Tree* t, Table* tb, const int64_t* active, int64_t A, int
   a.J = J;
   if (A > 1) {
     const size_t need = size_t(A) * (sizeof(uint64_t) + sizeof(int));
-    if (t->order_bytes < need) {
-      if (t->order_buf) cudaFreeAsync(t->order_buf, st);
-      t->order_buf = nullptr;
-      t->order_bytes = 0;
-      cudaError_t e = cudaMallocAsync(&t->order_buf, need, st);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(receiver order)");
-      t->order_bytes = need;
-    }
+    T2_CHECK(grow_buffer(&t->order_buf, &t->order_bytes, need, st, "receiver order"));
     uint64_t* keys = static_cast<uint64_t*>(t->order_buf);
     int* slots = reinterpret_cast<int*>(keys + A);
     k_order_keys<<<unsigned((A + 255) / 256), 256, 0, st>>>(active, A, t->N, t->inv, keys, slots);
@@ -1050,14 +1057,7 @@ static int launch_walk(Tree* t, Table* tb, const int64_t* active, int64_t A, int
   blocks = std::max<int64_t>(blocks, 1);
   const size_t warps = size_t(blocks) * kWalkWarps;
   const size_t need = walk_buffer_bytes(warps, a.M);
-  if (t->scratch_bytes < need) {
-    if (t->scratch) cudaFreeAsync(t->scratch, st);
-    t->scratch = nullptr;
-    t->scratch_bytes = 0;
-    cudaError_t e = cudaMallocAsync(&t->scratch, need, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(walk buffers)");
-    t->scratch_bytes = need;
-  }
+  T2_CHECK(grow_buffer(&t->scratch, &t->scratch_bytes, need, st, "walk buffers"));
   place_walk_buffers(static_cast<char*>(t->scratch), warps, a.M, &a.srcU, &a.srcV, &a.srcT, &a.pixU);
   T2_CUDA(cudaMemsetAsync(t->counter, 0, sizeof(unsigned long long), st));
   void* args[] = {&a};
@@ -1171,18 +1171,18 @@ static int ensure_csm(Tree* t, Table* tb, cudaStream_t st) {
   const int npix = 12 * tb->nside * tb->nside, P = npix / 2;
   const int64_t n = t->n_nodes;
   const size_t ntau = size_t(n) * npix * t->nbp, nd = size_t(n) * npix;
-  for (float** p : {&tb->csm_tau, &tb->csm_d}) {
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(p),
-                                    (p == &tb->csm_tau ? ntau : nd) * sizeof(float), st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(complex source model)");
-  }
-  {
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tb->csm_anti), npix * sizeof(int), st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(complex source model)");
-  }
-  T2_CUDA(cudaMemsetAsync(tb->csm_tau, 0, ntau * sizeof(float), st));
-  T2_CUDA(cudaMemsetAsync(tb->csm_d, 0, nd * sizeof(float), st));
-  k_csm_anti<<<(npix + 127) / 128, 128, 0, st>>>(tb->nside, npix, tb->dirs64, tb->csm_anti);
+  // built in temporaries and kept by the table only when complete
+  DeviceTemp<float> csm_tau(st), csm_d(st);
+  DeviceTemp<int> csm_anti(st);
+  T2_CHECK(device_alloc(reinterpret_cast<void**>(&csm_tau.p), ntau * sizeof(float), st,
+                        "complex source model tables"));
+  T2_CHECK(device_alloc(reinterpret_cast<void**>(&csm_d.p), nd * sizeof(float), st,
+                        "complex source model tables"));
+  T2_CHECK(device_alloc(reinterpret_cast<void**>(&csm_anti.p), npix * sizeof(int), st,
+                        "complex source model tables"));
+  T2_CUDA(cudaMemsetAsync(csm_tau.p, 0, ntau * sizeof(float), st));
+  T2_CUDA(cudaMemsetAsync(csm_d.p, 0, nd * sizeof(float), st));
+  k_csm_anti<<<(npix + 127) / 128, 128, 0, st>>>(tb->nside, npix, tb->dirs64, csm_anti.p);
   note_launch();
   for (int d = t->max_depth; d >= 0; --d) {
     const int64_t lb = t->level_begin[d], le = t->level_begin[d + 1];
@@ -1190,13 +1190,18 @@ static int ensure_csm(Tree* t, Table* tb, cudaStream_t st) {
     if (work <= 0) continue;
     const unsigned blocks = unsigned((work + 255) / 256);
     switch (t->nbp) {
-      case 1: k_csm_level<1><<<blocks, 256, 0, st>>>(lb, le, npix, P, t->nodes, t->csrc, t->Lnode, t->alpha_leaf, tb->alpha, tb->dirs, tb->csm_d, tb->csm_tau); break;
-      case 2: k_csm_level<2><<<blocks, 256, 0, st>>>(lb, le, npix, P, t->nodes, t->csrc, t->Lnode, t->alpha_leaf, tb->alpha, tb->dirs, tb->csm_d, tb->csm_tau); break;
-      default: k_csm_level<4><<<blocks, 256, 0, st>>>(lb, le, npix, P, t->nodes, t->csrc, t->Lnode, t->alpha_leaf, tb->alpha, tb->dirs, tb->csm_d, tb->csm_tau); break;
+      case 1: k_csm_level<1><<<blocks, 256, 0, st>>>(lb, le, npix, P, t->nodes, t->csrc, t->Lnode, t->alpha_leaf, tb->alpha, tb->dirs, csm_d.p, csm_tau.p); break;
+      case 2: k_csm_level<2><<<blocks, 256, 0, st>>>(lb, le, npix, P, t->nodes, t->csrc, t->Lnode, t->alpha_leaf, tb->alpha, tb->dirs, csm_d.p, csm_tau.p); break;
+      default: k_csm_level<4><<<blocks, 256, 0, st>>>(lb, le, npix, P, t->nodes, t->csrc, t->Lnode, t->alpha_leaf, tb->alpha, tb->dirs, csm_d.p, csm_tau.p); break;
     }
     note_launch();
   }
   T2_CUDA(cudaGetLastError());
+  tb->csm_tau = csm_tau.p;
+  tb->csm_d = csm_d.p;
+  tb->csm_anti = csm_anti.p;
+  csm_tau.p = csm_d.p = nullptr;
+  csm_anti.p = nullptr;
   return TREVR2_OK;
 }
 
@@ -1241,14 +1246,7 @@ static int launch_walk_bucket(Tree* t, Table* tb, const int64_t* active, int64_t
   a.A = A;
   a.J = J;
   const size_t need_order = size_t(A) * (sizeof(uint64_t) + 2 * sizeof(int));
-  if (t->order_bytes < need_order) {
-    if (t->order_buf) cudaFreeAsync(t->order_buf, st);
-    t->order_buf = nullptr;
-    t->order_bytes = 0;
-    cudaError_t e = cudaMallocAsync(&t->order_buf, need_order, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(receiver order)");
-    t->order_bytes = need_order;
-  }
+  T2_CHECK(grow_buffer(&t->order_buf, &t->order_bytes, need_order, st, "receiver order"));
   uint64_t* keys = static_cast<uint64_t*>(t->order_buf);
   int* slots = reinterpret_cast<int*>(keys + A);
   int* leaf = slots + A;
@@ -1295,14 +1293,7 @@ static int launch_walk_bucket(Tree* t, Table* tb, const int64_t* active, int64_t
   const size_t ob = (warps * kOriginWords * sizeof(double) + 255) & ~size_t(255);
   const size_t pb = warps * size_t(bk.pp_cap) * (3 * sizeof(float4) + sizeof(int));
   const size_t need = wb + ob + pb;
-  if (t->scratch_bytes < need) {
-    if (t->scratch) cudaFreeAsync(t->scratch, st);
-    t->scratch = nullptr;
-    t->scratch_bytes = 0;
-    cudaError_t e = cudaMallocAsync(&t->scratch, need, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(walk buffers)");
-    t->scratch_bytes = need;
-  }
+  T2_CHECK(grow_buffer(&t->scratch, &t->scratch_bytes, need, st, "walk buffers"));
   place_walk_buffers(static_cast<char*>(t->scratch), warps, a.M, &a.srcU, &a.srcV, &a.srcT, &a.pixU);
   a.origin64 = reinterpret_cast<double*>(static_cast<char*>(t->scratch) + wb);
   if (bk.pp) {
@@ -1460,6 +1451,7 @@ struct Batch {
   const void* fn = nullptr;  // kernel, shared memory and grid of that shape
   size_t smem = 0;
   int64_t blocks = 0;
+  bool ready = false;        // the shape covers every row (false after a failed autotune)
   cudaStream_t last_stream = nullptr;
   // per-bucket plans (TREVR2_BUCKET, with TREVR2_PP / TREVR2_CSM)
   bool bucket = false;
@@ -1469,17 +1461,19 @@ struct Batch {
   BatchArgs args;
 };
 
-// Grid and buffers of a batch launch for (warps, M); grows the buffers.
-static int batch_shape(Batch* b, int warps, int M, int64_t limit, const void** fn, size_t* smem,
-                       int64_t* blocks, cudaStream_t st) {
-  *fn = b->bucket ? bucket_batched_kernel(b->nbp, b->pp, b->csm) : walk_kernel(b->nbp, warps, true);
-  *smem = walk_smem(warps, b->args.stack_ints, b->args.npix, b->args.max_depth);
+// Selects the launch shape (warps, M) for the first `limit` rows: kernel,
+// grid and walk buffers (grown if needed).  Nothing changes unless it
+// succeeds: a larger buffer is allocated before the old one is released.
+static int batch_select(Batch* b, int warps, int M, int64_t limit, cudaStream_t st) {
+  const void* fn = b->bucket ? bucket_batched_kernel(b->nbp, b->pp, b->csm)
+                             : walk_kernel(b->nbp, warps, true);
+  const size_t smem = walk_smem(warps, b->args.stack_ints, b->args.npix, b->args.max_depth);
   int per_sm = 0, sms = 0;
-  T2_CHECK(config_walk_kernel(*fn, warps, *smem, &per_sm, &sms));
+  T2_CHECK(config_walk_kernel(fn, warps, smem, &per_sm, &sms));
   int64_t g = int64_t(sms) * per_sm;
   g = std::min<int64_t>(g, (limit + warps - 1) / warps);
-  *blocks = std::max<int64_t>(g, 1);
-  const size_t nw = size_t(*blocks) * warps;
+  const int64_t blocks = std::max<int64_t>(g, 1);
+  const size_t nw = size_t(blocks) * warps;
   // per-bucket plans: the warps' FP64 origin slots and p-p particle arrays
   const size_t wb = (walk_buffer_bytes(nw, M) + 255) & ~size_t(255);
   const size_t ob = b->bucket ? (nw * kOriginWords * sizeof(double) + 255) & ~size_t(255) : 0;
@@ -1487,11 +1481,10 @@ static int batch_shape(Batch* b, int warps, int M, int64_t limit, const void** f
   const size_t pb = nw * pp_cap * (3 * sizeof(float4) + sizeof(int));
   const size_t need = wb + ob + pb;
   if (b->scratch_bytes < need) {
+    void* fresh = nullptr;
+    T2_CHECK(device_alloc(&fresh, need, st, "batch walk buffers"));
     if (b->scratch) cudaFreeAsync(b->scratch, st);
-    b->scratch = nullptr;
-    b->scratch_bytes = 0;
-    cudaError_t e = cudaMallocAsync(&b->scratch, need, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(batch walk buffers)");
+    b->scratch = fresh;
     b->scratch_bytes = need;
   }
   place_walk_buffers(static_cast<char*>(b->scratch), nw, M, &b->args.srcU, &b->args.srcV,
@@ -1512,15 +1505,13 @@ static int batch_shape(Batch* b, int warps, int M, int64_t limit, const void** f
       bk.pp_si = b->pp ? reinterpret_cast<int*>(pp + 3 * nw * pp_cap) : nullptr;
     }
   }
-  return TREVR2_OK;
-}
-
-// Fixes the launch shape (warps, M) for the first `limit` receivers.
-static int batch_select(Batch* b, int warps, int M, int64_t limit, cudaStream_t st) {
-  T2_CHECK(batch_shape(b, warps, M, limit, &b->fn, &b->smem, &b->blocks, st));
+  b->fn = fn;
+  b->smem = smem;
+  b->blocks = blocks;
   b->warps = warps;
   b->M = M;
   b->args.total = limit;
+  b->ready = limit == b->total;
   return TREVR2_OK;
 }
 
@@ -1687,6 +1678,9 @@ extern "C" int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const 
   for (int i = 0; i < ntrees; ++i) {
     b->args.tree[i].max_depth = max_depth;
     b->args.tree[i].stack_ints = 64 * (max_depth + 2);
+    b->args.tree[i].src_stack_cap = b->args.tree[i].stack_ints;
+    if (const int cap = debug_source_stack_cap())
+      b->args.tree[i].src_stack_cap = std::min(cap, b->args.tree[i].stack_ints);
   }
   b->args.max_depth = max_depth;
   b->args.stack_ints = 64 * (max_depth + 2);
@@ -1712,8 +1706,8 @@ extern "C" int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const 
     const size_t bsort = up(radix_ws_bytes(int64_t(R))), bscan = up(4 * scan_ws_ints(int64_t(R)));
     const size_t bbuck = b->bucket ? bk * 2 + br : 0;  // usi, ubkey, uorder
     const size_t bytes = bk * 2 + br * 2 + bu + 256 + bsort + bscan + bbuck;
-    cudaError_t e = cudaMallocAsync(&b->dedup, bytes, st);
-    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMallocAsync(batch deduplication)"));
+    rc = device_alloc(&b->dedup, bytes, st, "batch deduplication buffers");
+    if (rc) return fail(rc);
     char* p = static_cast<char*>(b->dedup);
     b->args.keys = reinterpret_cast<uint64_t*>(p); p += bk;
     b->args.ukeys = reinterpret_cast<uint64_t*>(p); p += bk;
@@ -1768,6 +1762,12 @@ extern "C" int trevr2_batch_run(trevr2_batch* batch, const int64_t* active, floa
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   b->last_stream = st;
   if (b->total == 0) return TREVR2_OK;
+  if (!b->ready) {
+    set_error("trevr2_batch_run: the plan has no launch shape for all its rows (an earlier "
+              "trevr2_batch_autotune failed); call trevr2_batch_autotune again or create a "
+              "new plan");
+    return TREVR2_EINVAL;
+  }
   return batch_enqueue(b, active, J, st);
 }
 
@@ -1872,6 +1872,18 @@ extern "C" int trevr2_J_batched(trevr2_tree* const* trees, int ntrees, const int
   return rc;
 }
 
+extern "C" int trevr2_kernel_binary_version(int* version) {
+  clear_error();
+  if (!version) {
+    set_error("trevr2_kernel_binary_version: version is NULL");
+    return TREVR2_EINVAL;
+  }
+  cudaFuncAttributes attr;
+  T2_CUDA(cudaFuncGetAttributes(&attr, reinterpret_cast<const void*>(&k_walk<4, kWalkWarps>)));
+  *version = attr.binaryVersion;
+  return TREVR2_OK;
+}
+
 extern "C" int trevr2_status(trevr2_tree* tree, void* stream) {
   clear_error();
   if (!tree) {
@@ -1907,37 +1919,23 @@ extern "C" int trevr2_prepare(trevr2_tree* tree, int nside, void* stream) {
 // them the walk buffers come from one file-scope device array of fixed size
 // instead of the tree's grown-on-demand buffers.  Every process that loads
 // this library holds the array on every GPU it uses until it exits.
-#include <mutex>
-
 namespace trevr2 {
 
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB per device
 constexpr int kNoAllocSources = 256;  // source records per warp and pass
-constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
-
-// Device address of the array for the current device.  In host code the
-// array's name is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
+// Device address of the array on the current device.  In host code the
+// array's name is only a host-side stand-in, so its address is looked up,
+// with the device current, on every call: a cached address would go stale
+// if the device's context were reset and the module loaded again.  The
+// first lookup on a device loads the library's module there.
 static int noalloc_scratch(void** out) {
-  int dev = 0;
-  T2_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kNoAllocMaxDevices) {
-    set_error("trevr2_J_noalloc: device ordinal %d above %d", dev, kNoAllocMaxDevices - 1);
-    return TREVR2_EUNSUPPORTED;
-  }
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(walk scratch)");
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(walk scratch)");
+  *out = p;
   return TREVR2_OK;
 }
 

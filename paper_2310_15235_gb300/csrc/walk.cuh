@@ -57,6 +57,7 @@ struct WalkArgs {
                     // directed beam (unit vector, pixel or -1)
   int M;
   int stack_ints;   // per warp
+  int src_stack_cap;  // entries of the source cut's stack used (<= stack_ints)
   int max_depth;
   uint32_t* status;
   unsigned long long* counter;

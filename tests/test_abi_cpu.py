@@ -33,14 +33,6 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(lib.exported_symbols()) <= exported
 
 
-def test_library_targets_sm103a(lib):
-    out = subprocess.run(["cuobjdump", "--list-elf", lib.library_path()], capture_output=True,
-                         text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    assert "sm_103a" in out.stdout
-
-
 def test_last_error_without_gpu_work(lib):
     so = lib.load_library()
     # argument validation happens on the host before any CUDA call

@@ -215,6 +215,58 @@ def test_backward_full_size_sampled(t2, oracle_mod, adjoint_field):
     tree.free()
 
 
+def _central_differences(oracle_mod, case, act, w, params, step_rel=1e-6):
+    """FP64 central differences of the oracle's Loss = sum w J for each
+    (which, elem, band), a relative step of step_rel, the tree rebuilt per
+    evaluation; a parameter whose two one-sided differences disagree by more
+    than 10% (a discrete choice of the walk switched inside the step) is
+    returned as NaN."""
+    nside, theta = case["nside"], case["theta"]
+
+    def loss(c):
+        return float((oracle_mod.OracleTree.from_case(c).J(act, nside, theta) * w).sum())
+
+    base_loss = loss(case)
+    out = np.empty(len(params))
+    for k, (which, elem, band) in enumerate(params):
+        base = float(case[which][elem, band])
+        step = step_rel * base
+        vals = []
+        for sgn in (+1, -1):
+            c2 = dict(case)
+            a2 = case[which].astype(np.float64).copy()
+            a2[elem, band] = base + sgn * step
+            c2[which] = a2
+            vals.append(loss(c2))
+        fwd, bwd = (vals[0] - base_loss) / step, (base_loss - vals[1]) / step
+        agree = abs(fwd - bwd) <= 0.1 * max(abs(fwd), abs(bwd)) or max(abs(fwd), abs(bwd)) == 0.0
+        out[k] = (vals[0] - vals[1]) / (2 * step) if agree else np.nan
+    return out
+
+
+def test_backward_full_size_against_central_differences(t2, oracle_mod, adjoint_field):
+    """The same workload, receivers, weights and 64 parameters as above, with
+    the GPU gradient checked directly against FP64 central differences of
+    the oracle's loss (relative step 1e-6); parameters whose one-sided
+    differences disagree by more than 10% are skipped and counted."""
+    case = adjoint_field
+    tree = _gpu_tree(t2, case)
+    rng = np.random.default_rng(12)
+    act = np.sort(rng.choice(case["active"], 4096, replace=False))
+    w = rng.uniform(0.0, 1.0, size=(len(act), 2)).astype(np.float32)
+    gk, gl = tree.J_backward(act, w, case["nside"], case["theta"])
+    n_gas = int((case["mass"] > 0).sum())
+    src = np.flatnonzero(case["lum"].sum(1) > 0)
+    params = [("kappa", int(e), int(rng.integers(0, 2))) for e in rng.choice(n_gas, 32, False)]
+    params += [("lum", int(e), int(rng.integers(0, 2))) for e in rng.choice(src, 32, False)]
+    fd = _central_differences(oracle_mod, case, act, w.astype(np.float64), params)
+    keep = np.isfinite(fd)
+    assert keep.sum() >= 56, f"{int((~keep).sum())} of 64 parameters switched a discrete choice"
+    got = _gather(gk, gl, params)
+    _check(np.asarray(got)[keep], fd[keep], "adjoint full size vs central differences")
+    tree.free()
+
+
 def _line_case(n=1500, nb=2, seed=58):
     """Absorbing elements on a line along +x (a beam direction of nside 1)
     with a source at its far end: with theta -> 0 every leaf on the line is

@@ -95,3 +95,73 @@ def test_all_gas_sampled(t2, esc, cases, name):
     J_vac = esc.exact_J(case["pos"][gas[idx]], case["geometry"], absorb=False)
     _compare(J[idx], ref, J_vac, f"{name} all gas")
     tree.free()
+
+
+def _paper_rows():
+    import os
+    rows = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "escape_table.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            test, method, e, c = line.split()
+            rows[(test, method)] = (float(e) / 100.0, float(c))
+    return rows
+
+
+def test_table_escape_rows(t2, esc, cases):
+    """Every TREVR2 row of Table escape that this library reproduces: per
+    receiver and per bucket, transmission and linear averaging, p-p with
+    Eq. taucorr, directed rays, refinement (tau_refine = 0.01) and the complex
+    source model.  The GPU's escape fraction and covering factor on the
+    shell equal the oracle's; the rows are printed beside the paper's and the
+    exact answer (pytest -s)."""
+    BUCKET, PP, THICK, CSM = 16, 32, 2, 64
+    paper = _paper_rows()
+    keys = {"refined, per bucket": "refined",
+            "refined, directed, per bucket": "refined_directed",
+            "linear, refined, per bucket, 192 rays": "linear_refined_192",
+            "complex source, per bucket": "complex"}
+    lines = ["| test | average | escape GPU | oracle | paper | covering GPU | oracle | paper "
+             "| exact escape / covering |", "|---|---|---|---|---|---|---|---|---|"]
+    for name in NAMES:
+        case, ot = cases[name]
+        g = case["geometry"]
+        act = case["active"]
+        pts = case["pos"][act]
+        tree = _gpu_tree(t2, case)
+        e_x, c_x = esc.figures(esc.exact_J(pts, g), pts, g)
+        methods = [("transmission", 0), ("linear", LINEAR),
+                   ("transmission, per bucket", BUCKET),
+                   ("linear, per bucket", BUCKET | LINEAR),
+                   ("transmission, per bucket, p-p, thick", BUCKET | PP | THICK),
+                   ("linear, per bucket, p-p, thick", BUCKET | PP | THICK | LINEAR)]
+        if len(g["sources"]) == 1:  # directed rays aim at the one source
+            methods += [("directed, per bucket", BUCKET),
+                        ("directed, per bucket, p-p, thick", BUCKET | PP | THICK),
+                        ("refined, per bucket", BUCKET),
+                        ("refined, directed, per bucket", BUCKET)]
+        else:
+            methods += [("linear, refined, per bucket, 192 rays", BUCKET | LINEAR)]
+        methods += [("complex source, per bucket", BUCKET | CSM)]
+        for method, flags in methods:
+            tg = g["sources"][0] if "directed" in method else None
+            tau = 0.01 if "refined" in method else float("inf")
+            tree.set_tau_refine(tau)
+            ot.set_tau_refine(tau)
+            nside = 4 if "192" in method else case["nside"]
+            J = tree.J(act, nside, case["theta"], flags=flags, target=tg).cpu().numpy()[:, 0]
+            ref = ot.J(act, nside, case["theta"], flags=flags, target=tg)[:, 0]
+            e, c = esc.figures(J, pts, g)
+            e_o, c_o = esc.figures(ref, pts, g)
+            assert abs(e - e_o) <= 1e-5 * e_o, (name, method, e, e_o)
+            assert abs(c - c_o) <= 2.0 / len(act), (name, method, c, c_o)
+            pe, pc = paper.get((name, keys.get(method, method.split(",")[0])),
+                               (float("nan"), float("nan")))
+            lines.append(f"| {name} | {method} | {100 * e:.2f} % | {100 * e_o:.2f} % "
+                         f"| {100 * pe:.2f} % | {c:.3f} | {c_o:.3f} | {pc:.3f} "
+                         f"| {100 * e_x:.2f} % / {c_x:.3f} |")
+        tree.set_tau_refine(float("inf"))
+        ot.set_tau_refine(float("inf"))
+        tree.free()
+    print("\n" + "\n".join(lines))

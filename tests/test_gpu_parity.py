@@ -296,3 +296,9 @@ def test_J_receivers_on_root_faces(t2, oracle_mod, nside):
     ref = oracle_mod.OracleTree.from_case(case).J(act, nside, 0.75)
     _assert_J(J, ref, f"root faces nside={nside}")
     tree.free()
+
+
+def test_kernels_run_as_sm103a(t2):
+    """The loaded kernels are the sm_103a build (the library is compiled for
+    that architecture only)."""
+    assert t2.kernel_binary_version() == 103

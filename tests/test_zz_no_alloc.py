@@ -66,3 +66,21 @@ def test_noalloc_matches_allocating_entry_point(t2, theta, n_src):
         r = _rel(got, ref)
         assert np.median(r) <= 1e-4 and r.max() <= 1e-3, (call, np.median(r), r.max())
     tree.free()
+
+
+def test_noalloc_matches_oracle(t2, oracle_mod):
+    """The allocation-free walk against the FP64 oracle directly, on a small
+    case with ragged sizes, twice in a row, with and without SOFT | THICK."""
+    case = workloads.random_case(700, 35, nb=2, seed=33, clumped=True, n_active=301)
+    tree = t2.build(case["pos"], case["mass"], case["kappa"], case["lum"], case["h"],
+                    case["box_lo"], case["box_size"], case["bucket"])
+    tree.prepare(2)
+    ot = oracle_mod.OracleTree.from_case(case)
+    for flags in (0, 3):
+        ref = ot.J(case["active"], 2, 0.75, flags=flags)
+        for call in range(2):
+            rc, out = _noalloc(t2, tree, case["active"], 2, 0.75, 2, flags)
+            assert rc == 0, t2.load_library().trevr2_last_error()
+            r = _rel(out.cpu().numpy(), ref)
+            assert np.median(r) <= 1e-4 and r.max() <= 1e-3, (flags, call, np.median(r), r.max())
+    tree.free()
