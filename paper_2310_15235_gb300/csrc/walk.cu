@@ -304,6 +304,10 @@ struct BucketArgs {
   float4* pp_kc;         // [warps][pp_cap] kappa_b m 3 / (pi h^2) per band
   int* pp_si;            // [warps][pp_cap] sorted element index
   float4* pp_w;          // [warps][pp_cap] per receiver: x_k - x, |x_k - x|^2 - h_k^2
+  float4* pp_u;          // [warps][pp_cap] per receiver: unit x_k - x, cap threshold
+  uint32_t* pp_mask;     // [warps][kCubeCells][pp_cap / 32] per receiver: the p-p
+                         // particles that can meet a segment whose direction lies
+                         // in each direction cell
   // directed rays (Sec. 3.4.1): the beam holding the target points at it
   int directed;
   double target[3];      // normalised
@@ -437,86 +441,210 @@ __device__ int collect_pp(const WalkArgs& a, const BucketArgs& bk, const double*
   return n;
 }
 
-// The p-p optical depth, per band, of the segment from a receiver at x
-// (sorted index si) to a source at p (its element sj, or -1), v = p - x,
-// r = |v|: every p-p particle k other than those two that is closer to the
-// source than the receiver and within h_k of the segment (distance b) adds
-// kappa_k 3 m_k / (pi h_k^2) (1 - b / h_k).  pw[k] = (w, |w|^2 - h_k^2) with
-// w = x_k - x, set per receiver: with t the clamped segment parameter of
-// the closest point, |w|^2 - b^2 = t (2 w.v - t r^2), so most particles are
-// rejected with one load and a few products.  The column goes to zero at
-// b = h_k, so that test needs no care; "closer" is decided in FP32 and again
-// in FP64 (positions pos64 of the receiver, p64 of the source) inside a
-// guard band that covers the FP32 error.
-template <int NBP>
-__device__ __forceinline__ void pp_tau(const WalkArgs& a, int npp, const float4* pw,
-                                       const float4* xh, const float4* kc, const int* psi,
-                                       int si, float4 p, const double* p64, int sj, float vx,
-                                       float vy, float vz, float r, float* tau) {
-  const float r2 = r * r;
-  const float ir2 = 1.0f / r2;
-  const float guard = 2e-6f * r + 1e-7f;
-#pragma unroll 4
-  for (int k = 0; k < npp; ++k) {
-    const float4 w = pw[k];
-    const float dot = w.x * vx + w.y * vy + w.z * vz;
-    const float t = fminf(fmaxf(dot * ir2, 0.0f), 1.0f);
-    const float g = t * (2.0f * dot - t * r2);  // |w|^2 - b^2
-    if (!(g > w.w)) continue;                   // b >= h_k
-    const int kk = psi[k];
-    if (kk == si || kk == sj) continue;
-    const float4 q = xh[k];
-    const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
-    const float dj2 = dx * dx + dy * dy + dz * dz;
-    bool front;
-    if (fabsf(r2 - dj2) > guard * (r + sqrtf(dj2))) {
-      front = dj2 < r2;
-    } else {  // FP64: |x_k - p| < |x - p|
-      const double* xk = a.pos64 + 3 * int64_t(kk);
-      const double* xi = a.pos64 + 3 * int64_t(si);
-      double d2k = 0.0, d2i = 0.0;
-      for (int c = 0; c < 3; ++c) {
-        const double dk = __dsub_rn(xk[c], p64[c]);
-        const double di = __dsub_rn(xi[c], p64[c]);
-        d2k = __dadd_rn(d2k, __dmul_rn(dk, dk));
-        d2i = __dadd_rn(d2i, __dmul_rn(di, di));
-      }
-      front = sqrt(d2k) < sqrt(d2i);
-    }
-    if (!front) continue;
-    const float b2 = fmaxf(0.0f, (w.w + q.w * q.w) - g);
-    const float f = fmaxf(0.0f, 1.0f - sqrtf(b2) / q.w);
-    const float4 c = kc[k];
-    const float cv[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-    for (int bb = 0; bb < NBP; ++bb) tau[bb] += cv[bb] * f;
+// Direction cells that cull the p-p particles per source: the six faces of
+// the cube, each cut into 4 x 4 squares, projected onto the sphere.  Every
+// cell lies within 0.3398 rad of its centre direction; the cap tests use
+// 0.345 rad, a bound with a margin far above FP32 rounding.
+constexpr int kCubeCells = 96;
+constexpr float kCubeCosR = 0.941075452606513f;    // cos(0.345)
+constexpr float kCubeSinR = 0.33819667724779123f;  // sin(0.345)
+
+// The cell holding direction v (any length > 0).
+__device__ __forceinline__ int cube_cell(float vx, float vy, float vz) {
+  const float ax = fabsf(vx), ay = fabsf(vy), az = fabsf(vz);
+  int m;
+  float vm, ca, cb;
+  if (ax >= ay && ax >= az) {
+    m = 0; vm = vx; ca = vy; cb = vz;
+  } else if (ay >= az) {
+    m = 1; vm = vy; ca = vx; cb = vz;
+  } else {
+    m = 2; vm = vz; ca = vx; cb = vy;
   }
+  const float inv = 1.0f / fabsf(vm);
+  const int i = min(3, max(0, int((ca * inv + 1.0f) * 2.0f)));
+  const int j = min(3, max(0, int((cb * inv + 1.0f) * 2.0f)));
+  return (2 * m + (vm < 0.0f ? 1 : 0)) * 16 + i * 4 + j;
+}
+
+// The unit centre direction of cell c.
+__device__ __forceinline__ float3 cube_centre(int c) {
+  const int f = c >> 4, m = f >> 1;
+  const float sgn = (f & 1) ? -1.0f : 1.0f;
+  const float ca = -0.75f + 0.5f * float((c >> 2) & 3), cb = -0.75f + 0.5f * float(c & 3);
+  const float n = rsqrtf(1.0f + ca * ca + cb * cb);
+  if (m == 0) return make_float3(sgn * n, ca * n, cb * n);
+  if (m == 1) return make_float3(ca * n, sgn * n, cb * n);
+  return make_float3(ca * n, cb * n, sgn * n);
+}
+
+// Seen from the receiver, p-p particle k can only come within h_k of a
+// segment whose direction v makes an angle below beta_k = asin(h_k / |w_k|)
+// with w_k = x_k - x (or, with the receiver inside its disc, in any
+// direction; the clamped ends of the segment stay inside the same cap).
+// Per receiver, mask[c][g] bit i marks the particles 32 g + i whose cap,
+// widened by the cell bound, reaches cell c; pu[k] holds w_k / |w_k| and
+// cos(beta_k + bound).  Each lane owns cells lane, lane + 32, lane + 64.
+__device__ __forceinline__ void pp_cull_masks(int npp, int lane, const float4* pw,
+                                              const float4* xh, float4* pu, uint32_t* mask) {
+  const int W = (npp + 31) >> 5;
+  for (int k = lane; k < npp; k += 32) {
+    const float4 w = pw[k];
+    const float hk = xh[k].w;
+    const float D2 = w.x * w.x + w.y * w.y + w.z * w.z;
+    float4 u = make_float4(0.0f, 0.0f, 0.0f, -2.0f);  // every direction
+    if (D2 > hk * hk * (1.0f + 1e-4f)) {
+      const float iD = rsqrtf(D2);
+      const float sb = fminf(1.0f, hk * iD), cb = sqrtf(fmaxf(0.0f, 1.0f - sb * sb));
+      u = make_float4(w.x * iD, w.y * iD, w.z * iD, cb * kCubeCosR - sb * kCubeSinR);
+    }
+    pu[k] = u;
+  }
+  __syncwarp();
+  const float3 c0 = cube_centre(lane), c1 = cube_centre(lane + 32), c2 = cube_centre(lane + 64);
+  for (int g = 0; g < W; ++g) {
+    uint32_t m0 = 0, m1 = 0, m2 = 0;
+    const int kn = min(32, npp - 32 * g);
+    for (int i = 0; i < kn; ++i) {
+      const float4 u = pu[32 * g + i];
+      m0 |= uint32_t(u.x * c0.x + u.y * c0.y + u.z * c0.z >= u.w) << i;
+      m1 |= uint32_t(u.x * c1.x + u.y * c1.y + u.z * c1.z >= u.w) << i;
+      m2 |= uint32_t(u.x * c2.x + u.y * c2.y + u.z * c2.z >= u.w) << i;
+    }
+    mask[lane * W + g] = m0;
+    mask[(lane + 32) * W + g] = m1;
+    mask[(lane + 64) * W + g] = m2;
+  }
+  __syncwarp();
+}
+
+// What pp_term reads of p-p particle k: its offset from the receiver, its
+// position and h, its column factors per band, its sorted index.
+struct PPData {
+  float4 w, q, c;
+  int kk;
+};
+
+__device__ __forceinline__ PPData pp_load(int k, const float4* pw, const float4* xh,
+                                          const float4* kc, const int* psi) {
+  PPData d;
+  d.w = pw[k];
+  d.kk = psi[k];
+  d.q = xh[k];
+  d.c = kc[k];
+  return d;
+}
+
+// One p-p particle k's optical depth, per band, added to tau for the
+// segment from a receiver at x (sorted index si) to a source at p (its
+// element sj, or -1), v = p - x, r2 = |v|^2: the particle counts when it is
+// neither of the two, lies closer to the source than the receiver and
+// within h_k of the segment (distance b), and adds kappa_k 3 m_k /
+// (pi h_k^2) (1 - b / h_k).  pw[k] = (w, |w|^2 - h_k^2) with w = x_k - x,
+// set per receiver: with t the clamped segment parameter of the closest
+// point, |w|^2 - b^2 = t (2 w.v - t r^2).  The column goes to zero at
+// b = h_k, so that test needs no care; "closer" is decided in FP32 and
+// again in FP64 (positions pos64 of the receiver, p64 of the source) inside
+// a guard band that covers the FP32 error.  Lanes that are not live (no
+// source) add zero.
+template <int NBP>
+__device__ __forceinline__ void pp_term(const WalkArgs& a, const PPData& d, bool live, int si,
+                                        float4 p, const double* p64, int sj, float vx, float vy,
+                                        float vz, float r, float r2, float ir2, float guard,
+                                        float* tau) {
+  const float4 w = d.w;
+  const int kk = d.kk;
+  const float4 q = d.q;
+  const float4 c = d.c;
+  const float dot = w.x * vx + w.y * vy + w.z * vz;
+  const float t = fminf(fmaxf(dot * ir2, 0.0f), 1.0f);
+  const float g = t * (2.0f * dot - t * r2);  // |w|^2 - b^2
+  bool hit = live && (g > w.w) && kk != si && kk != sj;  // b < h_k, not the pair itself
+  const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+  const float dj2 = dx * dx + dy * dy + dz * dz;
+  const bool clear = fabsf(r2 - dj2) > guard * (r + sqrtf(dj2));
+  bool front = dj2 < r2;
+  if (hit && !clear) {  // FP64: |x_k - p| < |x - p|
+    const double* xk = a.pos64 + 3 * int64_t(kk);
+    const double* xi = a.pos64 + 3 * int64_t(si);
+    double d2k = 0.0, d2i = 0.0;
+    for (int cc = 0; cc < 3; ++cc) {
+      const double dk = __dsub_rn(xk[cc], p64[cc]);
+      const double di = __dsub_rn(xi[cc], p64[cc]);
+      d2k = __dadd_rn(d2k, __dmul_rn(dk, dk));
+      d2i = __dadd_rn(d2i, __dmul_rn(di, di));
+    }
+    front = sqrt(d2k) < sqrt(d2i);
+  }
+  hit = hit && front;
+  const float b2 = fmaxf(0.0f, (w.w + q.w * q.w) - g);
+  const float f = hit ? fmaxf(0.0f, 1.0f - sqrtf(b2) / q.w) : 0.0f;
+  const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+  for (int bb = 0; bb < NBP; ++bb) tau[bb] += cv[bb] * f;
+}
+
+// The n staged sources of a bucket in the order of their direction cell
+// seen from the bucket centre o, into perm (a stable counting sort: cell,
+// then index), so that the 32 sources a warp evaluates together point in
+// few directions.  cnt is shared memory of at least kCubeCells ints; with
+// fewer (nside 1) the order is left as it is.
+__device__ __forceinline__ void sort_sources_by_cell(const WalkArgs& a, int lane,
+                                                     const SrcEntry* V, int n, float3 o,
+                                                     int* cnt, int cnt_ints, int* perm) {
+  if (cnt_ints < kCubeCells) {
+    for (int e = lane; e < n; e += 32) perm[e] = e;
+    __syncwarp();
+    return;
+  }
+  auto cell_of = [&](int e) {
+    const int ref = V[e].ref;
+    const float4 pj = (ref & kRefElement) ? a.pos32[ref & 0x7fffffff] : a.csrc[ref];
+    return cube_cell(pj.x - o.x, pj.y - o.y, pj.z - o.z);
+  };
+  for (int c = lane; c < kCubeCells; c += 32) cnt[c] = 0;
+  __syncwarp();
+  for (int e = lane; e < n; e += 32) atomicAdd(&cnt[cell_of(e)], 1);
+  __syncwarp();
+  const int c0 = 3 * lane;  // 96 = 3 x 32 cells
+  const int s0 = cnt[c0], s1 = cnt[c0 + 1], s2 = cnt[c0 + 2];
+  const int incl = warp_incl_scan(s0 + s1 + s2, lane);
+  const int base = incl - (s0 + s1 + s2);
+  __syncwarp();
+  cnt[c0] = base;
+  cnt[c0 + 1] = base + s0;
+  cnt[c0 + 2] = base + s0 + s1;
+  __syncwarp();
+  const unsigned lt = (1u << lane) - 1u;
+  for (int e0 = 0; e0 < n; e0 += 32) {
+    const int e = e0 + lane;
+    const bool in = e < n;
+    const int c = in ? cell_of(e) : kCubeCells + lane;  // idle lanes match nothing
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    const int rank = __popc(peers & lt);
+    const int slot = in ? cnt[c] + rank : 0;
+    __syncwarp();
+    if (in && rank == 0) cnt[c] += __popc(peers);
+    __syncwarp();
+    if (in) perm[slot] = e;
+  }
+  __syncwarp();
 }
 
 // The staged sources against the bucket's receivers (one per lane j < nrec,
 // position xr, size hr, sorted index sir): per receiver, all lanes over the
 // sources with a compensated FP32 sum, reduced in FP64 into acc of lane j.
-// With kPP the npp p-p particles add their optical depth (pp_tau).
-template <int NBP, bool kPP>
+// (Without p-p absorption; eval_bucket_pp adds it.)
+template <int NBP>
 __device__ __forceinline__ void eval_bucket(const WalkArgs& a, bool soft, int lane,
                                             const SrcEntry* V, const float* T, int n, int nrec,
-                                            float4 xr, float hr, int sir, double* acc,
-                                            int npp, const float4* ppxh, const float4* ppkc,
-                                            const int* ppsi, float4* ppw) {
+                                            float4 xr, float hr, int sir, double* acc) {
   for (int j = 0; j < nrec; ++j) {
     const float xx = __shfl_sync(0xffffffffu, xr.x, j);
     const float xy = __shfl_sync(0xffffffffu, xr.y, j);
     const float xz = __shfl_sync(0xffffffffu, xr.z, j);
     const float hh = __shfl_sync(0xffffffffu, hr, j);
     const int si = __shfl_sync(0xffffffffu, sir, j);
-    if constexpr (kPP) {  // the p-p particles seen from this receiver
-      for (int k = lane; k < npp; k += 32) {
-        const float4 q = ppxh[k];
-        const float wx = q.x - xx, wy = q.y - xy, wz = q.z - xz;
-        ppw[k] = make_float4(wx, wy, wz, (wx * wx + wy * wy + wz * wz) - q.w * q.w);
-      }
-      __syncwarp();
-    }
     float Js[NBP], Jc[NBP];
 #pragma unroll
     for (int b = 0; b < NBP; ++b) Js[b] = Jc[b] = 0.0f;
@@ -530,19 +658,12 @@ __device__ __forceinline__ void eval_bucket(const WalkArgs& a, bool soft, int la
       if (!(r2 > 0.0f)) continue;  // the receiver itself, or on top of it
       const float r = sqrtf(r2);
       const float w = soft ? soft_kernel(r, hh) : 1.0f / (kFourPi * r2);
-      float tpp[NBP];
-#pragma unroll
-      for (int b = 0; b < NBP; ++b) tpp[b] = 0.0f;
-      if constexpr (kPP)
-        pp_tau<NBP>(a, npp, ppw, ppxh, ppkc, ppsi, si, p,
-                    elem ? a.pos64 + 3 * id : a.c64 + 3 * id, elem ? int(id) : -1, vx, vy, vz,
-                    r, tpp);
       const float rs = r / src.w;  // w: the source's projected distance
       const BandVec<NBP> L = load_bands<NBP>(elem ? a.Lelem + id * NBP : a.Lnode + id * NBP);
       const BandVec<NBP> tk = load_bands<NBP>(T + int64_t(e) * NBP);
 #pragma unroll
       for (int b = 0; b < NBP; ++b) {
-        const float term = L.v[b] * w * expf(-(tk.v[b] * rs + tpp[b]));
+        const float term = L.v[b] * w * expf(-(tk.v[b] * rs));
         const float y = term - Jc[b];
         const float t = Js[b] + y;
         Jc[b] = (t - Js[b]) - y;
@@ -556,7 +677,108 @@ __device__ __forceinline__ void eval_bucket(const WalkArgs& a, bool soft, int la
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if (lane == j) acc[b] += v;
     }
-    if constexpr (kPP) __syncwarp();  // ppw is rewritten for the next receiver
+  }
+}
+
+// eval_bucket with the p-p absorption of Sec. 2.4.  Per receiver the p-p
+// particles' offsets and direction masks are set up (pp_cull_masks); the
+// sources, in the order perm (grouped by direction cell), are evaluated 32
+// at a time.  A group walks, in increasing k, the particles that the
+// direction cell of any of its sources can reach: for each source these
+// include every particle that can absorb on its segment, and the others
+// add nothing, so each source's p-p optical depth is the sum over all
+// particles in index order.
+template <int NBP>
+__device__ __forceinline__ void eval_bucket_pp(const WalkArgs& a, bool soft, int lane,
+                                               const SrcEntry* V, const float* T, const int* perm,
+                                               int n, int nrec, float4 xr, float hr, int sir,
+                                               double* acc, int npp, const float4* ppxh,
+                                               const float4* ppkc, const int* ppsi, float4* ppw,
+                                               float4* ppu, uint32_t* ppmask) {
+  const int W = (npp + 31) >> 5;
+  for (int j = 0; j < nrec; ++j) {
+    const float xx = __shfl_sync(0xffffffffu, xr.x, j);
+    const float xy = __shfl_sync(0xffffffffu, xr.y, j);
+    const float xz = __shfl_sync(0xffffffffu, xr.z, j);
+    const float hh = __shfl_sync(0xffffffffu, hr, j);
+    const int si = __shfl_sync(0xffffffffu, sir, j);
+    for (int k = lane; k < npp; k += 32) {  // the p-p particles seen from this receiver
+      const float4 q = ppxh[k];
+      const float wx = q.x - xx, wy = q.y - xy, wz = q.z - xz;
+      ppw[k] = make_float4(wx, wy, wz, (wx * wx + wy * wy + wz * wz) - q.w * q.w);
+    }
+    __syncwarp();
+    pp_cull_masks(npp, lane, ppw, ppxh, ppu, ppmask);
+    float Js[NBP], Jc[NBP];
+#pragma unroll
+    for (int b = 0; b < NBP; ++b) Js[b] = Jc[b] = 0.0f;
+    for (int e0 = 0; e0 < n; e0 += 32) {
+      const int e = e0 + lane < n ? perm[e0 + lane] : -1;
+      bool live = false, elem = false;
+      int64_t id = 0;
+      float4 p = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      float vx = 0.0f, vy = 0.0f, vz = 0.0f, r = 1.0f, w = 0.0f, s_proj = 1.0f;
+      if (e >= 0) {
+        const SrcEntry src = V[e];
+        elem = (src.ref & kRefElement) != 0;
+        id = src.ref & 0x7fffffff;
+        p = elem ? a.pos32[id] : a.csrc[id];
+        vx = p.x - xx;
+        vy = p.y - xy;
+        vz = p.z - xz;
+        const float rr = vx * vx + vy * vy + vz * vz;
+        live = rr > 0.0f;  // else the receiver itself, or on top of it
+        if (live) {
+          r = sqrtf(rr);
+          w = soft ? soft_kernel(r, hh) : 1.0f / (kFourPi * rr);
+          s_proj = src.w;  // the source's projected distance
+        }
+      }
+      const float r2 = r * r, ir2 = 1.0f / r2, guard = 2e-6f * r + 1e-7f;
+      const double* p64 = elem ? a.pos64 + 3 * id : a.c64 + 3 * id;
+      const int sj = elem ? int(id) : -1;
+      const int cell = live ? cube_cell(vx, vy, vz) : 0;
+      float tpp[NBP];
+#pragma unroll
+      for (int b = 0; b < NBP; ++b) tpp[b] = 0.0f;
+      for (int g = 0; g < W; ++g) {
+        uint32_t bits = live ? ppmask[cell * W + g] : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+        while (bits) {  // two particles at a time: both loads in flight together
+          const int k0 = 32 * g + __ffs(bits) - 1;
+          bits &= bits - 1u;
+          const bool two = bits != 0u;
+          const int k1 = two ? 32 * g + __ffs(bits) - 1 : k0;
+          if (two) bits &= bits - 1u;
+          const PPData d0 = pp_load(k0, ppw, ppxh, ppkc, ppsi);
+          const PPData d1 = pp_load(k1, ppw, ppxh, ppkc, ppsi);
+          pp_term<NBP>(a, d0, live, si, p, p64, sj, vx, vy, vz, r, r2, ir2, guard, tpp);
+          if (two) pp_term<NBP>(a, d1, live, si, p, p64, sj, vx, vy, vz, r, r2, ir2, guard, tpp);
+        }
+      }
+      if (live) {
+        const float rs = r / s_proj;
+        const BandVec<NBP> L = load_bands<NBP>(elem ? a.Lelem + id * NBP : a.Lnode + id * NBP);
+        const BandVec<NBP> tk = load_bands<NBP>(T + int64_t(e) * NBP);
+#pragma unroll
+        for (int b = 0; b < NBP; ++b) {
+          const float term = L.v[b] * w * expf(-(tk.v[b] * rs + tpp[b]));
+          const float y = term - Jc[b];
+          const float t = Js[b] + y;
+          Jc[b] = (t - Js[b]) - y;
+          Js[b] = t;
+        }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < NBP; ++b) {
+      double v = double(Js[b]) - double(Jc[b]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == j) acc[b] += v;
+    }
+    __syncwarp();  // ppw, ppu, ppmask are rewritten for the next receiver
   }
 }
 
@@ -616,6 +838,8 @@ __device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0,
   const float4* ppkc = bk.pp_kc + gw * bk.pp_cap;
   const int* ppsi = bk.pp_si + gw * bk.pp_cap;
   float4* ppw = bk.pp_w + gw * bk.pp_cap;
+  float4* ppu = bk.pp_u + gw * bk.pp_cap;
+  uint32_t* ppmask = bk.pp_mask + gw * int64_t(kCubeCells) * (bk.pp_cap / 32);
   for (int64_t c0 = p0; c0 < p1; c0 += 32) {
     const int nrec = int(min(int64_t(32), p1 - c0));
     int si = -1;
@@ -643,8 +867,14 @@ __device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0,
         phase_absorb<NBP, true, kPP, kCSM>(a, o, si_o, lane, lstk, V, T, off, order, nbeams,
                                            next_beam, chain, leaf, rpp);
         __syncwarp();
-        eval_bucket<NBP, kPP>(a, soft, lane, V, T, n, nrec, xr, hr, si, acc, npp, ppxh, ppkc,
-                              ppsi, ppw);
+        if constexpr (kPP) {
+          // Up, the staged records' beams, is free once they are binned
+          sort_sources_by_cell(a, lane, V, n, o, off, 2 * a.npix + 32, Up);
+          eval_bucket_pp<NBP>(a, soft, lane, V, T, Up, n, nrec, xr, hr, si, acc, npp, ppxh, ppkc,
+                              ppsi, ppw, ppu, ppmask);
+        } else {
+          eval_bucket<NBP>(a, soft, lane, V, T, n, nrec, xr, hr, si, acc);
+        }
         __syncwarp();
       }
       if (lo + a.M >= total) break;
@@ -670,8 +900,13 @@ __device__ void walk_bucket(const WalkArgs& a, const BucketArgs& bk, int64_t p0,
 }
 
 // One warp per bucket; slots from a global counter.
+// Blocks per SM the per-bucket walk with p-p absorption is compiled for:
+// its particle loop holds two particles' loads in flight, and 5 blocks (96
+// registers a thread) measured faster than 7 (72, spilling) and than 4 or 6.
+constexpr int kPPBlocksPerSM = 5;
+
 template <int NBP, int WARPS, bool kPP, bool kCSM>
-__global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS)
+__global__ void __launch_bounds__(WARPS * 32, kPP ? kPPBlocksPerSM : kWalkWarpsPerSM / WARPS)
     k_walk_bucket(WalkArgs a, const __grid_constant__ BucketArgs bk) {
   extern __shared__ int smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -869,7 +1104,7 @@ __global__ void k_batch_leaf(const __grid_constant__ BatchArgs B,
 // many subsets and snapshots); slots from a global counter, a bucket walked
 // by the warp that takes its first slot.
 template <int NBP, int WARPS, bool kPP, bool kCSM>
-__global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS)
+__global__ void __launch_bounds__(WARPS * 32, kPP ? kPPBlocksPerSM : kWalkWarpsPerSM / WARPS)
     k_walk_bucket_batched(const __grid_constant__ BatchArgs B,
                           const __grid_constant__ BucketBatchArgs bb) {
   extern __shared__ int smem[];
@@ -1291,7 +1526,8 @@ static int launch_walk_bucket(Tree* t, Table* tb, const int64_t* active, int64_t
   const size_t warps = size_t(blocks) * kWalkWarps;
   const size_t wb = (walk_buffer_bytes(warps, a.M) + 255) & ~size_t(255);
   const size_t ob = (warps * kOriginWords * sizeof(double) + 255) & ~size_t(255);
-  const size_t pb = warps * size_t(bk.pp_cap) * (3 * sizeof(float4) + sizeof(int));
+  const size_t pb = warps * size_t(bk.pp_cap) *
+                    (4 * sizeof(float4) + sizeof(int) + kCubeCells / 32 * sizeof(uint32_t));
   const size_t need = wb + ob + pb;
   T2_CHECK(grow_buffer(&t->scratch, &t->scratch_bytes, need, st, "walk buffers"));
   place_walk_buffers(static_cast<char*>(t->scratch), warps, a.M, &a.srcU, &a.srcV, &a.srcT, &a.pixU);
@@ -1301,7 +1537,9 @@ static int launch_walk_bucket(Tree* t, Table* tb, const int64_t* active, int64_t
     bk.pp_xh = reinterpret_cast<float4*>(pp);
     bk.pp_kc = bk.pp_xh + warps * bk.pp_cap;
     bk.pp_w = bk.pp_kc + warps * bk.pp_cap;
-    bk.pp_si = reinterpret_cast<int*>(bk.pp_w + warps * bk.pp_cap);
+    bk.pp_u = bk.pp_w + warps * bk.pp_cap;
+    bk.pp_si = reinterpret_cast<int*>(bk.pp_u + warps * bk.pp_cap);
+    bk.pp_mask = reinterpret_cast<uint32_t*>(bk.pp_si + warps * bk.pp_cap);
   }
   T2_CUDA(cudaMemsetAsync(t->counter, 0, sizeof(unsigned long long), st));
   void* args[] = {&a, &bk};
@@ -1478,7 +1716,8 @@ static int batch_select(Batch* b, int warps, int M, int64_t limit, cudaStream_t 
   const size_t wb = (walk_buffer_bytes(nw, M) + 255) & ~size_t(255);
   const size_t ob = b->bucket ? (nw * kOriginWords * sizeof(double) + 255) & ~size_t(255) : 0;
   const size_t pp_cap = b->pp ? kPPCapacity : 0;
-  const size_t pb = nw * pp_cap * (3 * sizeof(float4) + sizeof(int));
+  const size_t pb = nw * pp_cap *
+                    (4 * sizeof(float4) + sizeof(int) + kCubeCells / 32 * sizeof(uint32_t));
   const size_t need = wb + ob + pb;
   if (b->scratch_bytes < need) {
     void* fresh = nullptr;
@@ -1502,7 +1741,11 @@ static int batch_select(Batch* b, int warps, int M, int64_t limit, cudaStream_t 
       bk.pp_xh = b->pp ? pp : nullptr;
       bk.pp_kc = b->pp ? pp + nw * pp_cap : nullptr;
       bk.pp_w = b->pp ? pp + 2 * nw * pp_cap : nullptr;
-      bk.pp_si = b->pp ? reinterpret_cast<int*>(pp + 3 * nw * pp_cap) : nullptr;
+      bk.pp_u = b->pp ? pp + 3 * nw * pp_cap : nullptr;
+      bk.pp_si = b->pp ? reinterpret_cast<int*>(pp + 4 * nw * pp_cap) : nullptr;
+      bk.pp_mask = b->pp ? reinterpret_cast<uint32_t*>(reinterpret_cast<int*>(pp + 4 * nw * pp_cap) +
+                                                      nw * pp_cap)
+                         : nullptr;
     }
   }
   b->fn = fn;
