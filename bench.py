@@ -33,11 +33,46 @@ import workloads  # noqa: E402
 METRIC = "active receiver x HEALPix-ray x band / s"
 UNIT = "receiver*ray*band/s"
 NODE_BYTES = 32  # walk record of one node
-# DRAM bytes (read + write) per receiver of one k_walk launch, from the ncu
-# capture of the 96^3 version of the benchmark field (2.42 GB read + 8.12 GB
-# written for 884,736 receivers); scaled by the receivers of a launch.  It
-# must be measured again (or set to None) whenever the walk kernel changes.
-WALK_TRAFFIC_BYTES_PER_RECEIVER = 11915.0
+# The ncu summary of the walk kernel on the 96^3 version of the benchmark
+# field records its DRAM bytes per launch and a hash of the sources the
+# kernel is compiled from; the bench scales the bytes by receivers, and only
+# while the sources still hash the same.
+WALK_PROFILE = os.path.join(ROOT, "profiles", "k_walk_clumpy96.md")
+WALK_SOURCES = ["walk.cu", "walk.cuh", "healpix.cuh", "internal.cuh"]
+
+
+def kernel_sources_sha256():
+    """SHA-256 over the sources compiled into the walk kernel (and the ABI
+    header they include)."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2310_15235_gb300", "csrc")
+    for name in WALK_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    with open(os.path.join(ROOT, "include", "trevr2.h"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()
+
+
+def _walk_traffic(receivers):
+    """(DRAM bytes of one walk launch over `receivers` scaled from the
+    profile's capture, note); bytes is None when the profile is missing or
+    was taken on other kernel sources."""
+    import re
+    try:
+        with open(WALK_PROFILE) as f:
+            m = re.search(r"<!-- traffic (\{.*?\}) -->", f.read())
+        rec = json.loads(m.group(1))
+    except Exception:
+        return None, "no machine-readable traffic record in the walk profile"
+    if rec.get("sources_sha256") != kernel_sources_sha256():
+        return None, ("the walk profile was captured on other kernel sources "
+                      f"(sha256 {rec.get('sources_sha256', '?')[:12]}); capture it again")
+    per = (rec["dram_read_bytes"] + rec["dram_write_bytes"]) / rec["receivers"]
+    return per * receivers, (f"ncu dram bytes of one k_walk launch on the {rec['field']} "
+                             f"({rec['receivers']:,} receivers), scaled by receivers; "
+                             f"profiles/k_walk_clumpy96.md")
 
 
 def _workload_name(case):
@@ -296,11 +331,10 @@ def run_ours(args, world, rank, local):
         ot, sample, st, t_j, t_build, cores = _oracle_sample(case, args.cpu_seconds)
         per_rec, means = _algorithmic_bytes_per_receiver(st, nb)
         achieved = per_rec * A / (walk_avg * 1e-3) / 1e9
+        traffic, traffic_note = _walk_traffic(A)
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved / hbm_peak,
-                    "traffic": (None if WALK_TRAFFIC_BYTES_PER_RECEIVER is None
-                                else WALK_TRAFFIC_BYTES_PER_RECEIVER * A),
-                    "traffic_note": "ncu dram bytes of the 96^3 field scaled by receivers",
+                    "frac": achieved / hbm_peak, "traffic": traffic,
+                    "traffic_note": traffic_note,
                     "kernel": "k_walk", "peak_kind": peak_kind,
                     "algorithmic_bytes_per_unit": per_rec / (npix * nb),
                     "per_receiver_counts": means}
