@@ -464,14 +464,18 @@ __device__ __forceinline__ int cube_cell(float vx, float vy, float vz) {
   const float inv = 1.0f / fabsf(vm);
   const int i = min(3, max(0, int((ca * inv + 1.0f) * 2.0f)));
   const int j = min(3, max(0, int((cb * inv + 1.0f) * 2.0f)));
-  return (2 * m + (vm < 0.0f ? 1 : 0)) * 16 + i * 4 + j;
+  // cells of a face in Morton order of (i, j): consecutive cells are neighbours
+  return (2 * m + (vm < 0.0f ? 1 : 0)) * 16 +
+         ((i & 1) | ((j & 1) << 1) | ((i & 2) << 1) | ((j & 2) << 2));
 }
 
 // The unit centre direction of cell c.
 __device__ __forceinline__ float3 cube_centre(int c) {
   const int f = c >> 4, m = f >> 1;
   const float sgn = (f & 1) ? -1.0f : 1.0f;
-  const float ca = -0.75f + 0.5f * float((c >> 2) & 3), cb = -0.75f + 0.5f * float(c & 3);
+  const int mo = c & 15;
+  const int ci = (mo & 1) | ((mo >> 1) & 2), cj = ((mo >> 1) & 1) | ((mo >> 2) & 2);
+  const float ca = -0.75f + 0.5f * float(ci), cb = -0.75f + 0.5f * float(cj);
   const float n = rsqrtf(1.0f + ca * ca + cb * cb);
   if (m == 0) return make_float3(sgn * n, ca * n, cb * n);
   if (m == 1) return make_float3(ca * n, sgn * n, cb * n);
@@ -546,7 +550,8 @@ __device__ __forceinline__ PPData pp_load(int k, const float4* pw, const float4*
 // b = h_k, so that test needs no care; "closer" is decided in FP32 and
 // again in FP64 (positions pos64 of the receiver, p64 of the source) inside
 // a guard band that covers the FP32 error.  Lanes that are not live (no
-// source) add zero.
+// source) add zero.  Every lane of the warp calls it for the same k (a vote
+// skips the rest when no lane's segment meets the particle).
 template <int NBP>
 __device__ __forceinline__ void pp_term(const WalkArgs& a, const PPData& d, bool live, int si,
                                         float4 p, const double* p64, int sj, float vx, float vy,
@@ -560,6 +565,7 @@ __device__ __forceinline__ void pp_term(const WalkArgs& a, const PPData& d, bool
   const float t = fminf(fmaxf(dot * ir2, 0.0f), 1.0f);
   const float g = t * (2.0f * dot - t * r2);  // |w|^2 - b^2
   bool hit = live && (g > w.w) && kk != si && kk != sj;  // b < h_k, not the pair itself
+  if (!__any_sync(0xffffffffu, hit)) return;  // no lane's segment meets the particle
   const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
   const float dj2 = dx * dx + dy * dy + dz * dz;
   const bool clear = fabsf(r2 - dj2) > guard * (r + sqrtf(dj2));
