@@ -55,10 +55,8 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
-def _walk_traffic(receivers):
-    """(DRAM bytes of one walk launch over `receivers` scaled from the
-    profile's capture, note); bytes is None when the profile is missing or
-    was taken on other kernel sources."""
+def _walk_profile_record():
+    """The walk profile's machine-readable record, or (None, why)."""
     import re
     try:
         with open(WALK_PROFILE) as f:
@@ -69,10 +67,36 @@ def _walk_traffic(receivers):
     if rec.get("sources_sha256") != kernel_sources_sha256():
         return None, ("the walk profile was captured on other kernel sources "
                       f"(sha256 {rec.get('sources_sha256', '?')[:12]}); capture it again")
+    return rec, None
+
+
+def _walk_traffic(receivers):
+    """(DRAM bytes of one walk launch over `receivers` scaled from the
+    profile's capture, note); bytes is None when the profile is missing or
+    was taken on other kernel sources."""
+    rec, why = _walk_profile_record()
+    if rec is None:
+        return None, why
     per = (rec["dram_read_bytes"] + rec["dram_write_bytes"]) / rec["receivers"]
     return per * receivers, (f"ncu dram bytes of one k_walk launch on the {rec['field']} "
                              f"({rec['receivers']:,} receivers), scaled by receivers; "
                              f"profiles/k_walk_clumpy96.md")
+
+
+def _walk_counters(hbm_peak):
+    """What the walk's ncu capture measured (SURVEY-style report: DRAM
+    throughput against the peak, L2 hit rate, warp execution efficiency,
+    issue-active share), or None."""
+    rec, _ = _walk_profile_record()
+    if rec is None or "duration_ms" not in rec:
+        return None
+    gbs = (rec["dram_read_bytes"] + rec["dram_write_bytes"]) / (rec["duration_ms"] * 1e-3) / 1e9
+    return {"field": rec["field"], "dram_gbs": gbs, "dram_frac": gbs / hbm_peak,
+            "l2_hit_pct": rec["l2_hit_pct"],
+            "warp_execution_efficiency": rec["lanes_active"] / 32.0,
+            "issue_active_pct": rec["issue_active_pct"],
+            "note": "ncu counters of one cold, serialised launch; the walk is bound by "
+                    "instruction issue, not by DRAM"}
 
 
 def _workload_name(case):
@@ -334,14 +358,19 @@ def run_ours(args, world, rank, local):
         traffic, traffic_note = _walk_traffic(A)
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved / hbm_peak, "traffic": traffic,
-                    "traffic_note": traffic_note,
+                    "traffic_note": traffic_note, "ncu": _walk_counters(hbm_peak),
                     "kernel": "k_walk", "peak_kind": peak_kind,
                     "algorithmic_bytes_per_unit": per_rec / (npix * nb),
                     "per_receiver_counts": means}
+        t0 = time.perf_counter()
+        ot.J(sample[:256], case["nside"], case["theta"], nthreads=1)
+        t_one = time.perf_counter() - t0
         cpu = {"value": len(sample) * npix * nb / t_j, "unit": UNIT, "cores": cores,
                "kind": "oracle",
                "sample": f"{len(sample)} random receivers of the same field (J walk only; "
-                         f"oracle tree+tables build {t_build:.1f} s not included)"}
+                         f"oracle tree+tables build {t_build:.1f} s not included)",
+               "single_thread": {"value": 256 * npix * nb / t_one, "unit": UNIT,
+                                 "sample": "256 of the same receivers on one thread"}}
         # sampled parity of this very run
         ref = ot.J(sample[:512], case["nside"], case["theta"], nthreads=cores)
         idx = sample[:512]  # active == arange for this workload
