@@ -443,6 +443,12 @@ def run_ours(args, world, rank, local):
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "clocks": clk,
+        "paper_context": {
+            "value": 1.104175e6 * 48 * 1 / 3.4, "unit": UNIT,
+            "note": "derived from the paper's Sec. 3.1 timing: one TREVR2 radiation step of "
+                    "the MUGS2 galaxy (1,104,175 gas, 48 rays, 1 band) in 3.4 s on 320 CPU "
+                    "cores, its per-bucket rays counted per receiver; another machine, "
+                    "workload and scheme, so context only"},
     }
     if world == 1 and not args.no_adjoint:
         line["adjoint"] = run_adjoint(args, dev)
