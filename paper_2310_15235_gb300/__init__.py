@@ -336,9 +336,11 @@ class Batch:
     Subset s owns rows offsets[s]..offsets[s+1]-1 of the concatenated receiver
     list and is walked in trees[tree_of[s]] (individual timesteps, Sec. 1.2;
     independent snapshots, Sec. 3.1).  Rows asking for the same receiver of
-    the same tree are walked once.  `run` enqueues a fixed sequence of kernels
-    with no allocation or synchronisation, so it can be recorded into a CUDA
-    graph and replayed.
+    the same tree are walked once; with flags=BUCKET (optionally | PP | CSM)
+    every distinct bucket of a tree is walked once for all the receivers the
+    subsets ask for.  `run` enqueues a fixed sequence of kernels with no
+    allocation or synchronisation, so it can be recorded into a CUDA graph and
+    replayed.
     """
 
     def __init__(self, trees, offsets, tree_of, nside: int = 2, theta: float = 0.75,

@@ -2,9 +2,13 @@
 sm_103a, loads, and exports every entry point the header declares."""
 
 import ctypes
+import os
+import re
 import subprocess
 
 import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
@@ -75,6 +79,23 @@ def test_flag_values_agree(lib):
         assert getattr(oracle, "FLAG_" + name) == defs[name], name
     bits = [defs[n] for n in ("SOFT", "THICK", "ASYNC", "LINEAR", "BUCKET", "PP", "CSM")]
     assert len(set(bits)) == len(bits) and all(b & (b - 1) == 0 for b in bits)
+
+
+def test_testing_aids_match_header(lib):
+    """The binding's testing-aid settings are the header's, and the library
+    rejects an unknown setting on the host (no GPU work)."""
+    with open(os.path.join(ROOT, "include", "trevr2.h")) as f:
+        hdr = f.read()
+    defs = {m.group(1): int(m.group(2)) for m in
+            re.finditer(r"#define TREVR2_(DEBUG_[A-Z_]+) (\d+)", hdr)}
+    assert defs == {"DEBUG_FAIL_ALLOC": lib.DEBUG_FAIL_ALLOC,
+                    "DEBUG_SOURCE_STACK": lib.DEBUG_SOURCE_STACK}
+    so = lib.load_library()
+    assert so.trevr2_debug_set(99, 0) == -1
+    assert b"unknown setting" in so.trevr2_last_error()
+    assert so.trevr2_debug_set(lib.DEBUG_FAIL_ALLOC, -1) == 0
+    assert so.trevr2_debug_pool_used(None) == -1
+    assert so.trevr2_kernel_binary_version(None) == -1
 
 
 def test_new_entry_points_validate_on_host(lib):
