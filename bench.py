@@ -84,9 +84,9 @@ def _walk_traffic(receivers):
 
 
 def _walk_counters(hbm_peak):
-    """What the walk's ncu capture measured (SURVEY-style report: DRAM
-    throughput against the peak, L2 hit rate, warp execution efficiency,
-    issue-active share), or None."""
+    """What the walk's ncu capture measured (DRAM throughput against the
+    peak, L2 hit rate, warp execution efficiency, issue-active share), or
+    None."""
     rec, _ = _walk_profile_record()
     if rec is None or "duration_ms" not in rec:
         return None
@@ -540,7 +540,7 @@ def run_batched(args, dev, per_receiver_bytes, per_bucket_walk_bytes, per_receiv
     clumpy 2M field, 64 subsets each of 10^U(2,6) receivers.  The batch is one
     autotuned persistent launch replayed from a CUDA graph; the comparison is
     one plain trevr2_J launch per subset on the same stream with the same
-    flags.  Measured per receiver (the benchmark spec's walk) and per bucket
+    flags.  Measured per receiver (the walk of trevr2_J) and per bucket
     (TREVR2_BUCKET, the paper's own scheme, where a run walks each distinct
     (snapshot, bucket) once)."""
     import torch
