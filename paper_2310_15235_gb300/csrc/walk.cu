@@ -993,6 +993,25 @@ struct BatchArgs {
   uint64_t* usi;                  // [total]
   uint64_t* ubkey;                // [total] tree << 32 | leaf (invalid: ntrees << 32)
   int* uorder;                    // [total] identity
+  int* tree_range;                // [ntrees + 1] first distinct key of each tree
+};
+
+// What one tree's launch of a batch run needs besides the tree's own walk
+// arguments: its range of the distinct keys, where their rows go, the walk
+// buffers and the work counter.
+struct BatchSlice {
+  const uint64_t* ukeys;
+  const uint64_t* ubkey;
+  const int* tree_range;
+  float* Ju;
+  int t;
+  int key_shift;
+  int nbsel;
+  SrcEntry* srcU;
+  int* pixU;
+  SrcEntry* srcV;
+  float* srcT;
+  unsigned long long* counter;
 };
 
 // Per-tree arguments of a per-bucket plan: the bucket walk's own arguments
@@ -1052,33 +1071,48 @@ __global__ void k_batch_scatter(const __grid_constant__ BatchArgs B) {
     B.J[r * B.nbsel + j] = ok ? B.Ju[u * B.nbsel + j] : __int_as_float(0x7fc00000);
 }
 
-// One warp per distinct valid key, keys from a global counter.
+// The range of each tree among the distinct keys (sorted by tree, invalid
+// receivers last): tree_range[t] is the first key of tree t or later.
+__global__ void k_batch_tree_range(const __grid_constant__ BatchArgs B) {
+  const int t = threadIdx.x;
+  if (t > B.ntrees) return;
+  int lo = 0, hi = *B.n_distinct;
+  const uint64_t key = uint64_t(t) << B.key_shift;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (B.ukeys[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  B.tree_range[t] = lo;
+}
+
+// One launch per tree (its walk arguments are this launch's own parameter,
+// so the walk reads them as directly as k_walk does): one warp per distinct
+// key of the tree, keys from a global counter.
 template <int NBP, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk_batched(const __grid_constant__ BatchArgs B) {
+__global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS)
+    k_walk_batched(WalkArgs a, const __grid_constant__ BatchSlice S) {
   extern __shared__ int smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;
-  int* wsm = smem + wib * (B.stack_ints + 2 * B.npix + 36 + 8 * (B.max_depth + 1));
+  int* wsm = smem + wib * (a.stack_ints + 2 * a.npix + 36 + 8 * (a.max_depth + 1));
   int* stk = wsm;
-  int* off = wsm + B.stack_ints;
-  int* next_beam = off + 2 * B.npix + 32;  // after the beam order and its counts
-  int* lstk = stk + lane * (B.max_depth + 2);
-  SrcEntry* U = B.srcU + gw * B.M;
-  int* Up = B.pixU + gw * B.M;
-  SrcEntry* V = B.srcV + gw * B.M;
-  float* T = B.srcT + gw * B.M * 4;
-  const unsigned long long nd = (unsigned long long)(*B.n_distinct);
+  int* off = wsm + a.stack_ints;
+  int* next_beam = off + 2 * a.npix + 32;  // after the beam order and its counts
+  int* lstk = stk + lane * (a.max_depth + 2);
+  SrcEntry* U = S.srcU + gw * a.M;
+  int* Up = S.pixU + gw * a.M;
+  SrcEntry* V = S.srcV + gw * a.M;
+  float* T = S.srcT + gw * a.M * 4;
+  const int64_t u0 = S.tree_range[S.t], u1 = S.tree_range[S.t + 1];
+  const uint64_t mask = (uint64_t(1) << S.key_shift) - 1;
   for (;;) {
-    unsigned long long u = 0;
-    if (lane == 0) u = atomicAdd(B.counter, 1ull);
-    u = __shfl_sync(0xffffffffu, u, 0);
-    if (u >= nd) break;
-    const uint64_t key = B.ukeys[u];
-    const int t = int(key >> B.key_shift);
-    if (t >= B.ntrees) break;  // invalid receivers sort last
-    const int si = int(key & ((uint64_t(1) << B.key_shift) - 1));
-    walk_receiver_si<NBP>(B.tree[t], si, B.Ju + int64_t(u) * B.nbsel, lane, stk, off, next_beam,
-                          lstk, U, Up, V, T);
+    unsigned long long slot = 0;
+    if (lane == 0) slot = atomicAdd(S.counter, 1ull);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    const int64_t u = u0 + int64_t(slot);
+    if (u >= u1) break;
+    walk_receiver_si<NBP>(a, int(S.ukeys[u] & mask), S.Ju + u * S.nbsel, lane, stk, off,
+                          next_beam, lstk, U, Up, V, T);
   }
 }
 
@@ -1106,40 +1140,39 @@ __global__ void k_batch_leaf(const __grid_constant__ BatchArgs B,
   B.usi[u] = uint64_t(si);
 }
 
-// One warp per bucket of distinct keys (the paper's per-bucket walk over
-// many subsets and snapshots); slots from a global counter, a bucket walked
-// by the warp that takes its first slot.
+// One warp per bucket of one tree's distinct keys (the paper's per-bucket
+// walk over many subsets and snapshots), one launch per tree as for
+// k_walk_batched; slots from a global counter, a bucket walked by the warp
+// that takes its first slot.
 template <int NBP, int WARPS, bool kPP, bool kCSM>
 __global__ void __launch_bounds__(WARPS * 32, kPP ? kPPBlocksPerSM : kWalkWarpsPerSM / WARPS)
-    k_walk_bucket_batched(const __grid_constant__ BatchArgs B,
-                          const __grid_constant__ BucketBatchArgs bb) {
+    k_walk_bucket_batched(WalkArgs a, const __grid_constant__ BucketArgs bk,
+                          const __grid_constant__ BatchSlice S) {
   extern __shared__ int smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;
-  int* wsm = smem + wib * (B.stack_ints + 2 * B.npix + 36 + 8 * (B.max_depth + 1));
+  int* wsm = smem + wib * (a.stack_ints + 2 * a.npix + 36 + 8 * (a.max_depth + 1));
   int* stk = wsm;
-  int* off = wsm + B.stack_ints;
-  int* next_beam = off + 2 * B.npix + 32;
-  int* lstk = stk + lane * (B.max_depth + 2);
-  SrcEntry* U = B.srcU + gw * B.M;
-  int* Up = B.pixU + gw * B.M;
-  SrcEntry* V = B.srcV + gw * B.M;
-  float* T = B.srcT + gw * B.M * 4;
-  const int64_t nd = *B.n_distinct;
+  int* off = wsm + a.stack_ints;
+  int* next_beam = off + 2 * a.npix + 32;
+  int* lstk = stk + lane * (a.max_depth + 2);
+  SrcEntry* U = S.srcU + gw * a.M;
+  int* Up = S.pixU + gw * a.M;
+  SrcEntry* V = S.srcV + gw * a.M;
+  float* T = S.srcT + gw * a.M * 4;
+  const int64_t u0 = S.tree_range[S.t], u1 = S.tree_range[S.t + 1];
   for (;;) {
     unsigned long long slot = 0;
-    if (lane == 0) slot = atomicAdd(B.counter, 1ull);
+    if (lane == 0) slot = atomicAdd(S.counter, 1ull);
     slot = __shfl_sync(0xffffffffu, slot, 0);
-    if (slot >= (unsigned long long)nd) break;
-    const int64_t p0 = int64_t(slot);
-    const uint64_t bkey = B.ubkey[p0];
-    const int t = int(bkey >> 32);
-    if (t >= B.ntrees) break;  // invalid receivers sort last
-    if (p0 > 0 && B.ubkey[p0 - 1] == bkey) continue;  // not the first slot of its bucket
+    const int64_t p0 = u0 + int64_t(slot);
+    if (p0 >= u1) break;
+    const uint64_t bkey = S.ubkey[p0];
+    if (p0 > u0 && S.ubkey[p0 - 1] == bkey) continue;  // not the first slot of its bucket
     int64_t p1 = p0 + 1;
     for (;;) {
       const int64_t p = p1 + lane;
-      const unsigned same = __ballot_sync(0xffffffffu, p < nd && B.ubkey[p] == bkey);
+      const unsigned same = __ballot_sync(0xffffffffu, p < u1 && S.ubkey[p] == bkey);
       if (same == 0xffffffffu) {
         p1 += 32;
         continue;
@@ -1147,8 +1180,8 @@ __global__ void __launch_bounds__(WARPS * 32, kPP ? kPPBlocksPerSM : kWalkWarpsP
       p1 += __ffs(~same) - 1;
       break;
     }
-    walk_bucket<NBP, kPP, kCSM>(B.tree[t], bb.tree[t], p0, p1, int(uint32_t(bkey)), gw, lane, stk,
-                                off, next_beam, lstk, U, Up, V, T);
+    walk_bucket<NBP, kPP, kCSM>(a, bk, p0, p1, int(uint32_t(bkey)), gw, lane, stk, off,
+                                next_beam, lstk, U, Up, V, T);
   }
 }
 
@@ -1782,15 +1815,35 @@ static int batch_enqueue(Batch* b, const int64_t* active, float* J, cudaStream_t
   if (b->bucket) {
     k_batch_leaf<<<g, 256, 0, st>>>(b->args, b->bb);
     note_launch();
-    void* argv[] = {&b->args, &b->bb};
-    T2_CUDA(cudaLaunchKernel(b->fn, dim3(unsigned(b->blocks)), dim3(b->warps * 32), argv, b->smem,
-                             st));
-  } else {
-    void* argv[] = {&b->args};
-    T2_CUDA(cudaLaunchKernel(b->fn, dim3(unsigned(b->blocks)), dim3(b->warps * 32), argv, b->smem,
-                             st));
   }
-  note_launch();
+  k_batch_tree_range<<<1, 64, 0, st>>>(b->args); note_launch();
+  // one walk launch per tree, each over that tree's distinct keys
+  BatchSlice sl;
+  sl.ukeys = b->args.ukeys;
+  sl.ubkey = b->args.ubkey;
+  sl.tree_range = b->args.tree_range;
+  sl.Ju = b->args.Ju;
+  sl.key_shift = b->args.key_shift;
+  sl.nbsel = b->args.nbsel;
+  sl.srcU = b->args.srcU;
+  sl.pixU = b->args.pixU;
+  sl.srcV = b->args.srcV;
+  sl.srcT = b->args.srcT;
+  sl.counter = b->counter;
+  for (int t = 0; t < b->args.ntrees; ++t) {
+    sl.t = t;
+    T2_CUDA(cudaMemsetAsync(b->counter, 0, sizeof(unsigned long long), st));
+    if (b->bucket) {
+      void* argv[] = {&b->args.tree[t], &b->bb.tree[t], &sl};
+      T2_CUDA(cudaLaunchKernel(b->fn, dim3(unsigned(b->blocks)), dim3(b->warps * 32), argv,
+                               b->smem, st));
+    } else {
+      void* argv[] = {&b->args.tree[t], &sl};
+      T2_CUDA(cudaLaunchKernel(b->fn, dim3(unsigned(b->blocks)), dim3(b->warps * 32), argv,
+                               b->smem, st));
+    }
+    note_launch();
+  }
   k_batch_scatter<<<g, 256, 0, st>>>(b->args); note_launch();
   T2_CUDA(cudaGetLastError());
   return TREVR2_OK;
@@ -1954,7 +2007,8 @@ extern "C" int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const 
     const size_t bk = up(8 * R), br = up(4 * R), bu = up(4 * R * nb);
     const size_t bsort = up(radix_ws_bytes(int64_t(R))), bscan = up(4 * scan_ws_ints(int64_t(R)));
     const size_t bbuck = b->bucket ? bk * 2 + br : 0;  // usi, ubkey, uorder
-    const size_t bytes = bk * 2 + br * 2 + bu + 256 + bsort + bscan + bbuck;
+    const size_t brange = up(sizeof(int) * (kMaxBatchTrees + 1));
+    const size_t bytes = bk * 2 + br * 2 + bu + 256 + bsort + bscan + bbuck + brange;
     rc = device_alloc(&b->dedup, bytes, st, "batch deduplication buffers");
     if (rc) return fail(rc);
     char* p = static_cast<char*>(b->dedup);
@@ -1966,6 +2020,7 @@ extern "C" int trevr2_batch_create(trevr2_tree* const* trees, int ntrees, const 
     b->args.n_distinct = reinterpret_cast<int*>(p); p += 256;
     b->sort_ws = p; p += bsort;
     b->scan_ws = reinterpret_cast<int*>(p); p += bscan;
+    b->args.tree_range = reinterpret_cast<int*>(p); p += brange;
     if (b->bucket) {
       b->args.usi = reinterpret_cast<uint64_t*>(p); p += bk;
       b->args.ubkey = reinterpret_cast<uint64_t*>(p); p += bk;
