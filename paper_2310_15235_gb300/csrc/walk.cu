@@ -78,6 +78,9 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
 #pragma unroll
     for (int c = 0; c < 3; ++c) inv[c] = n[c] != 0.0f ? 1.0f / n[c] : 0.0f;
     const float xv[3] = {x.x, x.y, x.z};
+    float nx[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) nx[c] = xv[c] * inv[c];
     float tau[NBP];
 #pragma unroll
     for (int b = 0; b < NBP; ++b) tau[b] = 0.0f;
@@ -102,11 +105,17 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
 #pragma unroll
       for (int b = 0; b < NBP; ++b) tau[b] += al.v[b] * (t1 - t0);
     };
+    // a pushed half carries the time the beam enters it (exactly its own slab
+    // entry time), so a pop only needs the exit time
+    int2* st2 = reinterpret_cast<int2*>(lstk);
+    bool up[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) up[c] = n[c] > 0.0f;
     int sp = 0;
     {
       const NodeW root = chain[0];
       float t0, t1;
-      bool go = (root.meta & kMetaHasAlpha) && beam_chord(root, xv, n, inv, smax, t0, t1);
+      bool go = (root.meta & kMetaHasAlpha) && beam_chord_fx(root, xv, n, inv, nx, smax, t0, t1);
       for (int kd = 0; go; ++kd) {
         const NodeW nd = chain[kd];
         if (nd.meta & kMetaLeaf) {
@@ -115,31 +124,46 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
         }
         bool lower_first, lower_hit, upper_hit;
         float lt0, lt1, ut0, ut1;
-        crossed_halves(nd, xv, n, inv, t0, t1, lower_first, lower_hit, upper_hit, lt0, lt1, ut0,
+        crossed_halves_fx(nd, xv, n, inv, nx, t0, t1, lower_first, lower_hit, upper_hit, lt0, lt1, ut0,
                        ut1);
         const bool near_hit = lower_first ? lower_hit : upper_hit;
         const bool far_hit = lower_first ? upper_hit : lower_hit;
-        if (far_hit) lstk[sp++] = lower_first ? nd.child + 1 : nd.child;
+        if (far_hit)
+          st2[sp++] = make_int2(lower_first ? nd.child + 1 : nd.child,
+                                __float_as_int(lower_first ? ut0 : lt0));
         go = near_hit;
         t0 = lower_first ? lt0 : ut0;
         t1 = lower_first ? lt1 : ut1;
       }
     }
     while (sp > 0 && ptr < end) {
-      const int q = lstk[--sp];
+      const int2 e = st2[--sp];
+      const int q = e.x;
+      const float t0 = __int_as_float(e.y);
       const NodeW nd = a.nodes[q];
-      float t0, t1;
-      if (!beam_chord(nd, xv, n, inv, smax, t0, t1)) continue;
+      float t1 = smax;
+      {
+        const float3 ex = node_ext(nd.meta);
+        const float ext3[3] = {ex.x, ex.y, ex.z};
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (n[c] != 0.0f)
+            t1 = fminf(t1, fmaf(up[c] ? nd.lo[c] + ext3[c] : nd.lo[c], inv[c], -nx[c]));
+      }
       if (!(nd.meta & kMetaLeaf) && cell_opens<kBucket, kPP>(a, q, nd, x, si, rpp)) {
         // the crossed halves, the near one (the side of the receiver) on top
         bool lower_first, lower_hit, upper_hit;
         float lt0, lt1, ut0, ut1;
-        crossed_halves(nd, xv, n, inv, t0, t1, lower_first, lower_hit, upper_hit, lt0, lt1, ut0,
+        crossed_halves_fx(nd, xv, n, inv, nx, t0, t1, lower_first, lower_hit, upper_hit, lt0, lt1, ut0,
                        ut1);
         const bool near_hit = lower_first ? lower_hit : upper_hit;
         const bool far_hit = lower_first ? upper_hit : lower_hit;
-        if (far_hit) lstk[sp++] = lower_first ? nd.child + 1 : nd.child;
-        if (near_hit) lstk[sp++] = lower_first ? nd.child : nd.child + 1;
+        if (far_hit)
+          st2[sp++] = make_int2(lower_first ? nd.child + 1 : nd.child,
+                                __float_as_int(lower_first ? ut0 : lt0));
+        if (near_hit)
+          st2[sp++] = make_int2(lower_first ? nd.child : nd.child + 1,
+                                __float_as_int(lower_first ? lt0 : ut0));
         continue;
       }
       segment(q, nd, t0, t1);
@@ -265,7 +289,7 @@ __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk(Wa
   int* stk = wsm;
   int* off = wsm + a.stack_ints;
   int* next_beam = off + 2 * a.npix + 32;  // after the beam order and its counts
-  int* lstk = stk + lane * (a.max_depth + 2);
+  int* lstk = stk + lane * 2 * (a.max_depth + 2);
   SrcEntry* U = a.srcU + gw * a.M;
   int* Up = a.pixU + gw * a.M;
   SrcEntry* V = a.srcV + gw * a.M;
@@ -921,7 +945,7 @@ __global__ void __launch_bounds__(WARPS * 32, kPP ? kPPBlocksPerSM : kWalkWarpsP
   int* stk = wsm;
   int* off = wsm + a.stack_ints;
   int* next_beam = off + 2 * a.npix + 32;
-  int* lstk = stk + lane * (a.max_depth + 2);
+  int* lstk = stk + lane * 2 * (a.max_depth + 2);
   SrcEntry* U = a.srcU + gw * a.M;
   int* Up = a.pixU + gw * a.M;
   SrcEntry* V = a.srcV + gw * a.M;
@@ -1098,7 +1122,7 @@ __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS)
   int* stk = wsm;
   int* off = wsm + a.stack_ints;
   int* next_beam = off + 2 * a.npix + 32;  // after the beam order and its counts
-  int* lstk = stk + lane * (a.max_depth + 2);
+  int* lstk = stk + lane * 2 * (a.max_depth + 2);
   SrcEntry* U = S.srcU + gw * a.M;
   int* Up = S.pixU + gw * a.M;
   SrcEntry* V = S.srcV + gw * a.M;
@@ -1155,7 +1179,7 @@ __global__ void __launch_bounds__(WARPS * 32, kPP ? kPPBlocksPerSM : kWalkWarpsP
   int* stk = wsm;
   int* off = wsm + a.stack_ints;
   int* next_beam = off + 2 * a.npix + 32;
-  int* lstk = stk + lane * (a.max_depth + 2);
+  int* lstk = stk + lane * 2 * (a.max_depth + 2);
   SrcEntry* U = S.srcU + gw * a.M;
   int* Up = S.pixU + gw * a.M;
   SrcEntry* V = S.srcV + gw * a.M;

@@ -69,9 +69,10 @@ struct WalkArgs {
 
 __device__ __forceinline__ float3 node_ext(uint32_t meta) {
   const int d = int(meta & kMetaDepthMask);
-  return make_float3(__int_as_float((127 - splits_on_axis(d, 0)) << 23),
-                     __int_as_float((127 - splits_on_axis(d, 1)) << 23),
-                     __int_as_float((127 - splits_on_axis(d, 2)) << 23));
+  const int q = (d * 21846) >> 16;  // d / 3 for d < 64
+  const int r = int((meta >> kMetaAxisShift) & 3u);  // d % 3
+  const float e = __int_as_float((127 - q) << 23);
+  return make_float3(r > 0 ? 0.5f * e : e, r > 1 ? 0.5f * e : e, e);
 }
 
 // Chord [t0, t1) of the beam x + t n (inv = 1/n, 0 where n = 0) with the box
@@ -126,6 +127,67 @@ __device__ __forceinline__ void crossed_halves(const NodeW& nd, const float xv[3
   } else {
     const float tm = (mid - xa) * ia;
     const float a1 = fminf(t1, tm), b0 = fmaxf(t0, tm);  // [t0, a1) before, [b0, t1) after
+    if (na > 0.0f) {
+      lt1 = a1;
+      ut0 = b0;
+    } else {
+      ut1 = a1;
+      lt0 = b0;
+    }
+    lower_hit = lt0 < lt1;
+    upper_hit = ut0 < ut1;
+  }
+  lower_hit &= (nd.meta & kMetaChild0Alpha) != 0;
+  upper_hit &= (nd.meta & kMetaChild1Alpha) != 0;
+}
+
+
+// Phase A forms: nx = x * inv per beam, slab times by one FMA per face.
+__device__ __forceinline__ bool beam_chord_fx(const NodeW& nd, const float xv[3], const float n[3],
+                                              const float inv[3], const float nx[3], float tmax,
+                                              float& t0, float& t1) {
+  const float3 e = node_ext(nd.meta);
+  const float ext[3] = {e.x, e.y, e.z};
+  t0 = 0.0f;
+  t1 = tmax;
+  bool hit = true;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float lo = nd.lo[c], hi = lo + ext[c];
+    if (n[c] == 0.0f) {
+      hit &= (lo <= xv[c]) && (xv[c] < hi);
+    } else {
+      const float ta = fmaf(lo, inv[c], -nx[c]), tb = fmaf(hi, inv[c], -nx[c]);
+      t0 = fmaxf(t0, fminf(ta, tb));
+      t1 = fminf(t1, fmaxf(ta, tb));
+    }
+  }
+  return hit && (t0 < t1);
+}
+
+__device__ __forceinline__ void crossed_halves_fx(const NodeW& nd, const float xv[3], const float n[3],
+                                                  const float inv[3], const float nx[3], float t0,
+                                                  float t1, bool& lower_first, bool& lower_hit,
+                                                  bool& upper_hit, float& lt0, float& lt1,
+                                                  float& ut0, float& ut1) {
+  const int axis = int((nd.meta >> kMetaAxisShift) & 3u);
+  const float3 e = node_ext(nd.meta);
+  const float lo = axis == 0 ? nd.lo[0] : (axis == 1 ? nd.lo[1] : nd.lo[2]);
+  const float ex = axis == 0 ? e.x : (axis == 1 ? e.y : e.z);
+  const float xa = axis == 0 ? xv[0] : (axis == 1 ? xv[1] : xv[2]);
+  const float na = axis == 0 ? n[0] : (axis == 1 ? n[1] : n[2]);
+  const float ia = axis == 0 ? inv[0] : (axis == 1 ? inv[1] : inv[2]);
+  const float nxa = axis == 0 ? nx[0] : (axis == 1 ? nx[1] : nx[2]);
+  const float mid = lo + 0.5f * ex;
+  lower_first = xa < mid;
+  lt0 = ut0 = t0;
+  lt1 = ut1 = t1;
+  if (na == 0.0f) {
+    lower_hit = lower_first;
+    upper_hit = !lower_first;
+  } else {
+    const float tm = fmaf(mid, ia, -nxa);
+    const float a1 = fminf(t1, tm), b0 = fmaxf(t0, tm);
     if (na > 0.0f) {
       lt1 = a1;
       ut0 = b0;
