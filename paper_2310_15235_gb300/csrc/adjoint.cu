@@ -214,9 +214,14 @@ __device__ void adjoint_stage1(const AdjArgs& g, float3 x, int si, int lane, int
     const float4 dn = a.dirs[k];
     const int pair = __float_as_int(dn.w);
     const float n[3] = {dn.x, dn.y, dn.z};
-    float inv[3];
+    float inv[3], nx[3];
+    bool up[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) inv[c] = n[c] != 0.0f ? 1.0f / n[c] : 0.0f;
+    for (int c = 0; c < 3; ++c) {
+      inv[c] = n[c] != 0.0f ? 1.0f / n[c] : 0.0f;
+      nx[c] = xv[c] * inv[c];
+      up[c] = n[c] > 0.0f;
+    }
     float tau[NBP];
 #pragma unroll
     for (int b = 0; b < NBP; ++b) tau[b] = 0.0f;
@@ -227,23 +232,45 @@ __device__ void adjoint_stage1(const AdjArgs& g, float3 x, int si, int lane, int
     const int first = nrec;
     int ptr = start;
     float s_next = V[ptr].s;
-    int sp = 1;
-    lstk[0] = 0;
+    // stack entries carry the time the beam enters the cell (a crossed half's
+    // entry time is exactly its own slab entry time), so a pop only needs the
+    // exit time; halves are pushed only when crossed and absorbing
+    int2* st2 = reinterpret_cast<int2*>(lstk);
+    int sp = 0;
+    {
+      const NodeW root = a.nodes[0];
+      float t0, t1;
+      if ((root.meta & kMetaHasAlpha) && beam_chord_fx(root, xv, n, inv, nx, smax, t0, t1))
+        st2[sp++] = make_int2(0, __float_as_int(t0));
+    }
     while (sp > 0 && ptr < end) {
-      const int q = lstk[--sp];
+      const int2 en = st2[--sp];
+      const int q = en.x;
+      const float t0 = __int_as_float(en.y);
       const NodeW nd = a.nodes[q];
-      if (!(nd.meta & kMetaHasAlpha)) continue;
-      float t0, t1, tx;
-      if (!beam_chord(nd, xv, n, inv, smax, t0, t1, tx)) continue;
+      float tx = INFINITY;
+      {
+        const float3 e3 = node_ext(nd.meta);
+        const float ext3[3] = {e3.x, e3.y, e3.z};
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (n[c] != 0.0f)
+            tx = fminf(tx, fmaf(up[c] ? nd.lo[c] + ext3[c] : nd.lo[c], inv[c], -nx[c]));
+      }
+      const float t1 = fminf(smax, tx);
       if (!(nd.meta & kMetaLeaf) && cell_opens(a, q, nd, x, si)) {
         bool lower_first, lower_hit, upper_hit;
         float lt0, lt1, ut0, ut1;
-        crossed_halves(nd, xv, n, inv, t0, t1, lower_first, lower_hit, upper_hit, lt0, lt1, ut0,
-                       ut1);
+        crossed_halves_fx(nd, xv, n, inv, nx, t0, t1, lower_first, lower_hit, upper_hit, lt0, lt1,
+                          ut0, ut1);
         const bool near_hit = lower_first ? lower_hit : upper_hit;
         const bool far_hit = lower_first ? upper_hit : lower_hit;
-        if (far_hit) lstk[sp++] = lower_first ? nd.child + 1 : nd.child;
-        if (near_hit) lstk[sp++] = lower_first ? nd.child : nd.child + 1;
+        if (far_hit)
+          st2[sp++] = make_int2(lower_first ? nd.child + 1 : nd.child,
+                                __float_as_int(lower_first ? ut0 : lt0));
+        if (near_hit)
+          st2[sp++] = make_int2(lower_first ? nd.child : nd.child + 1,
+                                __float_as_int(lower_first ? lt0 : ut0));
         continue;
       }
       const BandVec<NBP> al =
@@ -484,9 +511,10 @@ __device__ __forceinline__ void adjoint_receiver(const AdjArgs& g, int64_t slot,
 
 // Shared memory of an adjoint block: per warp the stacks, the beam offsets,
 // the beam records, the beam order and its 32 bucket counts, the next-beam
-// counter.
+// counter and one pad int (an even count keeps the lane stacks' 8-byte
+// entries aligned).
 inline size_t adjoint_smem(int warps, int stack_ints, int npix) {
-  return size_t(warps) * (stack_ints + 3 * npix + 33) * sizeof(int);
+  return size_t(warps) * (stack_ints + 3 * npix + 34) * sizeof(int);
 }
 
 template <int NBP, int WARPS>
@@ -495,12 +523,12 @@ __global__ void __launch_bounds__(WARPS * 32, kAdjBlocksPerSM) k_walk_adjoint(co
   const WalkArgs& a = g.w;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;
-  int* wsm = smem + wib * (a.stack_ints + 3 * a.npix + 33);
+  int* wsm = smem + wib * (a.stack_ints + 3 * a.npix + 34);  // even: 8-byte stack entries
   int* stk = wsm;
   int* off = wsm + a.stack_ints;
   uint32_t* binfo = reinterpret_cast<uint32_t*>(off + a.npix);
   int* next_beam = off + 3 * a.npix + 32;  // after the records, the order and its counts
-  int* lstk = stk + lane * (a.max_depth + 2);
+  int* lstk = stk + lane * 2 * (a.max_depth + 2);
   SrcEntry* U = a.srcU + gw * a.M;
   int* Up = a.pixU + gw * a.M;
   SrcEntry* V = a.srcV + gw * a.M;
