@@ -261,8 +261,8 @@ __device__ void adjoint_stage1(const AdjArgs& g, float3 x, int si, int lane, int
       if (!(nd.meta & kMetaLeaf) && cell_opens(a, q, nd, x, si)) {
         bool lower_first, lower_hit, upper_hit;
         float lt0, lt1, ut0, ut1;
-        crossed_halves_fx(nd, xv, n, inv, nx, t0, t1, lower_first, lower_hit, upper_hit, lt0, lt1,
-                          ut0, ut1);
+        crossed_halves_fx(nd, xv, n, inv, nx, node_ext(nd.meta).z, t0, t1, lower_first, lower_hit,
+                          upper_hit, lt0, lt1, ut0, ut1);
         const bool near_hit = lower_first ? lower_hit : upper_hit;
         const bool far_hit = lower_first ? upper_hit : lower_hit;
         if (far_hit)

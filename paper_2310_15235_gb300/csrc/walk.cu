@@ -47,6 +47,20 @@ __device__ __forceinline__ void add_csm(const WalkArgs& a, int ref, int k, BandV
   for (int b = 0; b < NBP; ++b) tk.v[b] += c.v[b];
 }
 
+// Box extents by depth (x, y, z; w = the split axis's, which is z's), the
+// same as node_ext, in shared memory: every kernel that runs phase A fills
+// it before its first receiver.
+__shared__ float4 g_ext_tab[64];
+
+__device__ __forceinline__ void init_ext_tab() {
+  if (threadIdx.x < 64) {
+    const uint32_t d = threadIdx.x;  // depth, and its split axis d mod 3
+    const float3 e = node_ext(d | ((d % 3u) << kMetaAxisShift));
+    g_ext_tab[threadIdx.x] = make_float4(e.x, e.y, e.z, e.z);
+  }
+  __syncthreads();
+}
+
 // Phase A: lanes take beams from the order above through a per-warp counter.
 // Each beam first descends the receiver's ancestors (chain[0..], root to the
 // receiver's leaf, in shared memory): they hold the receiver, so they open,
@@ -78,9 +92,14 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
 #pragma unroll
     for (int c = 0; c < 3; ++c) inv[c] = n[c] != 0.0f ? 1.0f / n[c] : 0.0f;
     const float xv[3] = {x.x, x.y, x.z};
-    float nx[3];
+    // slab times are face * inv - nx, one FMA; nx = -inf on an axis with
+    // n = 0 makes that axis's exit time +inf
+    float nx[3], upf[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) nx[c] = xv[c] * inv[c];
+    for (int c = 0; c < 3; ++c) {
+      nx[c] = n[c] != 0.0f ? xv[c] * inv[c] : -INFINITY;
+      upf[c] = n[c] > 0.0f ? 1.0f : 0.0f;  // the exit face is lo + upf * ext
+    }
     float tau[NBP];
 #pragma unroll
     for (int b = 0; b < NBP; ++b) tau[b] = 0.0f;
@@ -108,9 +127,6 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
     // a pushed half carries the time the beam enters it (exactly its own slab
     // entry time), so a pop only needs the exit time
     int2* st2 = reinterpret_cast<int2*>(lstk);
-    bool up[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) up[c] = n[c] > 0.0f;
     int sp = 0;
     {
       const NodeW root = chain[0];
@@ -124,8 +140,8 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
         }
         bool lower_first, lower_hit, upper_hit;
         float lt0, lt1, ut0, ut1;
-        crossed_halves_fx(nd, xv, n, inv, nx, t0, t1, lower_first, lower_hit, upper_hit, lt0, lt1, ut0,
-                       ut1);
+        crossed_halves_fx(nd, xv, n, inv, nx, g_ext_tab[nd.meta & kMetaDepthMask].w, t0, t1,
+                          lower_first, lower_hit, upper_hit, lt0, lt1, ut0, ut1);
         const bool near_hit = lower_first ? lower_hit : upper_hit;
         const bool far_hit = lower_first ? upper_hit : lower_hit;
         if (far_hit)
@@ -141,21 +157,18 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
       const int q = e.x;
       const float t0 = __int_as_float(e.y);
       const NodeW nd = a.nodes[q];
+      const float4 et = g_ext_tab[nd.meta & kMetaDepthMask];
       float t1 = smax;
-      {
-        const float3 ex = node_ext(nd.meta);
-        const float ext3[3] = {ex.x, ex.y, ex.z};
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          if (n[c] != 0.0f)
-            t1 = fminf(t1, fmaf(up[c] ? nd.lo[c] + ext3[c] : nd.lo[c], inv[c], -nx[c]));
-      }
-      if (!(nd.meta & kMetaLeaf) && cell_opens<kBucket, kPP>(a, q, nd, x, si, rpp)) {
+      t1 = fminf(t1, fmaf(fmaf(et.x, upf[0], nd.lo[0]), inv[0], -nx[0]));
+      t1 = fminf(t1, fmaf(fmaf(et.y, upf[1], nd.lo[1]), inv[1], -nx[1]));
+      t1 = fminf(t1, fmaf(fmaf(et.z, upf[2], nd.lo[2]), inv[2], -nx[2]));
+      if (!(nd.meta & kMetaLeaf) &&
+          cell_opens_e<kBucket, kPP>(a, q, nd, make_float3(et.x, et.y, et.z), x, si, rpp)) {
         // the crossed halves, the near one (the side of the receiver) on top
         bool lower_first, lower_hit, upper_hit;
         float lt0, lt1, ut0, ut1;
-        crossed_halves_fx(nd, xv, n, inv, nx, t0, t1, lower_first, lower_hit, upper_hit, lt0, lt1, ut0,
-                       ut1);
+        crossed_halves_fx(nd, xv, n, inv, nx, et.w, t0, t1, lower_first, lower_hit, upper_hit,
+                          lt0, lt1, ut0, ut1);
         const bool near_hit = lower_first ? lower_hit : upper_hit;
         const bool far_hit = lower_first ? upper_hit : lower_hit;
         if (far_hit)
@@ -282,6 +295,7 @@ __device__ __forceinline__ void walk_receiver(const WalkArgs& a, int64_t io, flo
 // One warp per receiver, receivers from a global counter.
 template <int NBP, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS) k_walk(WalkArgs a) {
+  init_ext_tab();
   extern __shared__ int smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;
@@ -938,6 +952,7 @@ constexpr int kPPBlocksPerSM = 5;
 template <int NBP, int WARPS, bool kPP, bool kCSM>
 __global__ void __launch_bounds__(WARPS * 32, kPP ? kPPBlocksPerSM : kWalkWarpsPerSM / WARPS)
     k_walk_bucket(WalkArgs a, const __grid_constant__ BucketArgs bk) {
+  init_ext_tab();
   extern __shared__ int smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;
@@ -1115,6 +1130,7 @@ __global__ void k_batch_tree_range(const __grid_constant__ BatchArgs B) {
 template <int NBP, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, kWalkWarpsPerSM / WARPS)
     k_walk_batched(WalkArgs a, const __grid_constant__ BatchSlice S) {
+  init_ext_tab();
   extern __shared__ int smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;
@@ -1172,6 +1188,7 @@ template <int NBP, int WARPS, bool kPP, bool kCSM>
 __global__ void __launch_bounds__(WARPS * 32, kPP ? kPPBlocksPerSM : kWalkWarpsPerSM / WARPS)
     k_walk_bucket_batched(WalkArgs a, const __grid_constant__ BucketArgs bk,
                           const __grid_constant__ BatchSlice S) {
+  init_ext_tab();
   extern __shared__ int smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = int64_t(blockIdx.x) * WARPS + wib;

@@ -165,15 +165,16 @@ __device__ __forceinline__ bool beam_chord_fx(const NodeW& nd, const float xv[3]
   return hit && (t0 < t1);
 }
 
+// ex is the node's extent along its split axis (node_ext(meta).z: the split
+// axis is the one bisected least often so far).  nx may be -inf on an axis
+// with n = 0; it is only read on the others.
 __device__ __forceinline__ void crossed_halves_fx(const NodeW& nd, const float xv[3], const float n[3],
-                                                  const float inv[3], const float nx[3], float t0,
-                                                  float t1, bool& lower_first, bool& lower_hit,
-                                                  bool& upper_hit, float& lt0, float& lt1,
-                                                  float& ut0, float& ut1) {
+                                                  const float inv[3], const float nx[3], float ex,
+                                                  float t0, float t1, bool& lower_first,
+                                                  bool& lower_hit, bool& upper_hit, float& lt0,
+                                                  float& lt1, float& ut0, float& ut1) {
   const int axis = int((nd.meta >> kMetaAxisShift) & 3u);
-  const float3 e = node_ext(nd.meta);
   const float lo = axis == 0 ? nd.lo[0] : (axis == 1 ? nd.lo[1] : nd.lo[2]);
-  const float ex = axis == 0 ? e.x : (axis == 1 ? e.y : e.z);
   const float xa = axis == 0 ? xv[0] : (axis == 1 ? xv[1] : xv[2]);
   const float na = axis == 0 ? n[0] : (axis == 1 ? n[1] : n[2]);
   const float ia = axis == 0 ? inv[0] : (axis == 1 ? inv[1] : inv[2]);
@@ -295,16 +296,16 @@ static __device__ __noinline__ bool box_within64(const double* __restrict__ x64,
 // Sec. 2.5.2: open iff d == 0 or B > theta d, seen from x (receiver si, or
 // with kBucket the centre of the bucket that warp -1 - si walks).  With
 // kPP and rpp > 0 (Sec. 2.4) a cell within the bucket's p-p radius opens
-// too; the FP64 radius is the fourth word of the warp's origin slot.
+// too; the FP64 radius is the fourth word of the warp's origin slot.  e is
+// the node's box extent.  d = 0 needs no test of its own: the margin is then
+// B^2 > 0, and inside the guard band the FP64 decision opens at d = 0.
 template <bool kBucket = false, bool kPP = false>
-__device__ __forceinline__ bool cell_opens(const WalkArgs& a, int q, const NodeW& nd, float3 x,
-                                           int si, float rpp = 0.0f) {
-  const float3 e = node_ext(nd.meta);
+__device__ __forceinline__ bool cell_opens_e(const WalkArgs& a, int q, const NodeW& nd, float3 e,
+                                             float3 x, int si, float rpp = 0.0f) {
   const float dx = fmaxf(0.0f, fmaxf(nd.lo[0] - x.x, x.x - (nd.lo[0] + e.x)));
   const float dy = fmaxf(0.0f, fmaxf(nd.lo[1] - x.y, x.y - (nd.lo[1] + e.y)));
   const float dz = fmaxf(0.0f, fmaxf(nd.lo[2] - x.z, x.z - (nd.lo[2] + e.z)));
   const float d2 = dx * dx + dy * dy + dz * dz;
-  if (d2 == 0.0f) return true;
   if constexpr (kBucket && kPP) {
     if (rpp > 0.0f) {
       const float m = d2 - rpp * rpp;
@@ -321,6 +322,12 @@ __device__ __forceinline__ bool cell_opens(const WalkArgs& a, int q, const NodeW
   const float g = 2.2f * B * (a.guard_abs + a.guard_rel * B);
   if (fabsf(margin) > g) return margin > 0.0f;
   return opens64(origin64<kBucket>(a, si), a.B64[q], a.theta64, nd.lo[0], nd.lo[1], nd.lo[2], nd.meta);
+}
+
+template <bool kBucket = false, bool kPP = false>
+__device__ __forceinline__ bool cell_opens(const WalkArgs& a, int q, const NodeW& nd, float3 x,
+                                           int si, float rpp = 0.0f) {
+  return cell_opens_e<kBucket, kPP>(a, q, nd, node_ext(nd.meta), x, si, rpp);
 }
 
 // Eq. intint as a kernel of r for an element of size h (normalised units).
