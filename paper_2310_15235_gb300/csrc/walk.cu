@@ -47,18 +47,23 @@ __device__ __forceinline__ void add_csm(const WalkArgs& a, int ref, int k, BandV
   for (int b = 0; b < NBP; ++b) tk.v[b] += c.v[b];
 }
 
-// Box extents by depth (x, y, z; w = the split axis's, which is z's), the
-// same as node_ext, in shared memory: every kernel that runs phase A fills
-// it before its first receiver.
-__shared__ float4 g_ext_tab[64];
+// Box extents for phase A's stack pops, the same values as node_ext: the
+// longest side 2^-floor(depth / 3) by depth in shared memory (256 bytes, so
+// that the walk kernels keep their blocks per SM), the others halved on the
+// axes already split at this depth.  x, y, z, and w = the split axis's extent
+// (z's).  Every kernel that runs phase A fills the table before its first
+// receiver.
+__shared__ float g_ext_e[64];
 
 __device__ __forceinline__ void init_ext_tab() {
-  if (threadIdx.x < 64) {
-    const uint32_t d = threadIdx.x;  // depth, and its split axis d mod 3
-    const float3 e = node_ext(d | ((d % 3u) << kMetaAxisShift));
-    g_ext_tab[threadIdx.x] = make_float4(e.x, e.y, e.z, e.z);
-  }
+  if (threadIdx.x < 64) g_ext_e[threadIdx.x] = __int_as_float((127 - int(threadIdx.x) / 3) << 23);
   __syncthreads();
+}
+
+__device__ __forceinline__ float4 ext_of(uint32_t meta) {
+  const float e = g_ext_e[meta & kMetaDepthMask];
+  const uint32_t r = (meta >> kMetaAxisShift) & 3u;
+  return make_float4(r > 0u ? 0.5f * e : e, r > 1u ? 0.5f * e : e, e, e);
 }
 
 // Phase A: lanes take beams from the order above through a per-warp counter.
@@ -140,7 +145,7 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
         }
         bool lower_first, lower_hit, upper_hit;
         float lt0, lt1, ut0, ut1;
-        crossed_halves_fx(nd, xv, n, inv, nx, g_ext_tab[nd.meta & kMetaDepthMask].w, t0, t1,
+        crossed_halves_fx(nd, xv, n, inv, nx, ext_of(nd.meta).w, t0, t1,
                           lower_first, lower_hit, upper_hit, lt0, lt1, ut0, ut1);
         const bool near_hit = lower_first ? lower_hit : upper_hit;
         const bool far_hit = lower_first ? upper_hit : lower_hit;
@@ -157,7 +162,7 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
       const int q = e.x;
       const float t0 = __int_as_float(e.y);
       const NodeW nd = a.nodes[q];
-      const float4 et = g_ext_tab[nd.meta & kMetaDepthMask];
+      const float4 et = ext_of(nd.meta);
       float t1 = smax;
       t1 = fminf(t1, fmaf(fmaf(et.x, upf[0], nd.lo[0]), inv[0], -nx[0]));
       t1 = fminf(t1, fmaf(fmaf(et.y, upf[1], nd.lo[1]), inv[1], -nx[1]));
