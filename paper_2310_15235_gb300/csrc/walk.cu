@@ -145,7 +145,7 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
         }
         bool lower_first, lower_hit, upper_hit;
         float lt0, lt1, ut0, ut1;
-        crossed_halves_fx(nd, xv, n, inv, nx, ext_of(nd.meta).w, t0, t1,
+        crossed_halves_fx<!kPP>(nd, xv, n, inv, nx, ext_of(nd.meta).w, t0, t1,
                           lower_first, lower_hit, upper_hit, lt0, lt1, ut0, ut1);
         const bool near_hit = lower_first ? lower_hit : upper_hit;
         const bool far_hit = lower_first ? upper_hit : lower_hit;
@@ -172,7 +172,7 @@ __device__ void phase_absorb(const WalkArgs& a, float3 x, int si, int lane, int*
         // the crossed halves, the near one (the side of the receiver) on top
         bool lower_first, lower_hit, upper_hit;
         float lt0, lt1, ut0, ut1;
-        crossed_halves_fx(nd, xv, n, inv, nx, et.w, t0, t1, lower_first, lower_hit, upper_hit,
+        crossed_halves_fx<!kPP>(nd, xv, n, inv, nx, et.w, t0, t1, lower_first, lower_hit, upper_hit,
                           lt0, lt1, ut0, ut1);
         const bool near_hit = lower_first ? lower_hit : upper_hit;
         const bool far_hit = lower_first ? upper_hit : lower_hit;

@@ -167,7 +167,11 @@ __device__ __forceinline__ bool beam_chord_fx(const NodeW& nd, const float xv[3]
 
 // ex is the node's extent along its split axis (node_ext(meta).z: the split
 // axis is the one bisected least often so far).  nx may be -inf on an axis
-// with n = 0; it is only read on the others.
+// with n = 0; it is only read on the others.  kBranchFree takes a grazing
+// beam (n = 0 on the split axis) through the same arithmetic as the others
+// (same decisions; faster, except in the p-p walk, which spills at its
+// register limit and keeps the branch).
+template <bool kBranchFree = true>
 __device__ __forceinline__ void crossed_halves_fx(const NodeW& nd, const float xv[3], const float n[3],
                                                   const float inv[3], const float nx[3], float ex,
                                                   float t0, float t1, bool& lower_first,
@@ -183,13 +187,15 @@ __device__ __forceinline__ void crossed_halves_fx(const NodeW& nd, const float x
   lower_first = xa < mid;
   lt0 = ut0 = t0;
   lt1 = ut1 = t1;
-  if (na == 0.0f) {
+  if (!kBranchFree && na == 0.0f) {
     lower_hit = lower_first;
     upper_hit = !lower_first;
   } else {
-    const float tm = fmaf(mid, ia, -nxa);
+    // a grazing beam (na = 0) never reaches the split plane: +inf on the
+    // receiver's side, -inf on the other, taken as a beam in +axis
+    const float tm = na != 0.0f ? fmaf(mid, ia, -nxa) : (lower_first ? INFINITY : -INFINITY);
     const float a1 = fminf(t1, tm), b0 = fmaxf(t0, tm);
-    if (na > 0.0f) {
+    if (na >= 0.0f) {
       lt1 = a1;
       ut0 = b0;
     } else {
