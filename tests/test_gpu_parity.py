@@ -298,6 +298,29 @@ def test_J_receivers_on_root_faces(t2, oracle_mod, nside):
     tree.free()
 
 
+@pytest.mark.parametrize("nside", [1, 2, 4])
+def test_J_receivers_on_split_planes(t2, oracle_mod, nside):
+    """Receivers exactly on internal split planes (dyadic coordinates, one or
+    two of them), seen along beams with zero components: such a beam lies in
+    the plane, and the half-open cells put it in the upper half only."""
+    case = workloads.random_case(1200, 30, nb=2, seed=25, clumped=True, n_active=300)
+    rng = np.random.default_rng(6)
+    planes = np.array([0.5, 0.25, 0.75, 0.125, 0.375, 0.625, 0.875])
+    moved = rng.choice(1200, 90, replace=False)
+    for j, i in enumerate(moved):
+        axes = rng.choice(3, 1 + j % 2, replace=False)
+        case["pos"][i, axes] = rng.choice(planes, len(axes))
+    act = np.unique(np.concatenate([case["active"], moved])).astype(np.int64)
+    tree = _gpu_tree(t2, case)
+    J = tree.J(act, nside, 0.75).cpu().numpy()
+    ref = oracle_mod.OracleTree.from_case(case).J(act, nside, 0.75)
+    _assert_J(J, ref, f"split planes nside={nside}")
+    Jb = tree.J(act, nside, 0.75, flags=16).cpu().numpy()
+    refb = oracle_mod.OracleTree.from_case(case).J(act, nside, 0.75, flags=16)
+    _assert_J(Jb, refb, f"split planes, per bucket, nside={nside}")
+    tree.free()
+
+
 def test_kernels_run_as_sm103a(t2):
     """The loaded kernels are the sm_103a build (the library is compiled for
     that architecture only)."""
